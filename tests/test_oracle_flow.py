@@ -1,0 +1,102 @@
+"""Flow-level pins of the oracle: invariants, symmetries, reduced-form equivalence and the
+free-molecular closed forms of diffuse-wall Fourier and Couette flow."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fdlb as ofd
+
+
+@pytest.mark.parametrize("qy,qz,grid", [(4, 4, "uniform"), (4, 0, "tanh"), (0, 0, "uniform"), (6, 4, "tanh")])
+def test_uniform_equilibrium_is_stationary(qy, qz, grid):
+    """Equal-temperature resting walls, no force: the uniform equilibrium is a steady state
+    (n_w = n0 by the +- symmetry of the nodes, zero gradients, J1 = 0, f^S = f)."""
+    o = ofd.Oracle(ofd.Params(nx=12, qx_half=4, qy=qy, qz=qz, kn=0.1, eta0=0.2, grid=grid))
+    f0 = o.f.copy()
+    o.step(30)
+    assert np.abs(o.f - f0).max() <= 1e-13 * np.abs(f0).max()
+
+
+@pytest.mark.parametrize("case", ["fourier", "couette", "poiseuille"])
+def test_mass_conservation(case):
+    """Diffuse walls with n_w from the zero-normal-flux condition conserve the total mass."""
+    kw = dict(fourier=dict(qy=4, qz=4, T_left=0.9, T_right=1.1),
+              couette=dict(qy=6, qz=0, U_left=-0.42, U_right=0.42, grid="tanh"),
+              poiseuille=dict(qy=6, qz=0, accel_y=0.05, grid="tanh"))[case]
+    o = ofd.Oracle(ofd.Params(nx=20, qx_half=4, kn=0.1, eta0=0.2, **kw))
+    m0 = o.mass()
+    o.step(150)
+    assert abs(o.mass() / m0 - 1.0) < 5e-14
+
+
+def test_mirror_symmetries():
+    """Couette: u_y odd, n and T even; Poiseuille: u_y even; Fourier with swapped walls: mirror image."""
+    o = ofd.Oracle(ofd.Params(nx=16, qx_half=4, qy=4, qz=0, kn=0.1, eta0=0.2, U_left=-0.42, U_right=0.42, grid="tanh"))
+    o.step(100)
+    M = o.moments()
+    np.testing.assert_allclose(M["uy"], -M["uy"][::-1], atol=1e-13)
+    np.testing.assert_allclose(M["n"], M["n"][::-1], rtol=1e-13)
+    np.testing.assert_allclose(M["T"], M["T"][::-1], rtol=1e-13)
+    p = ofd.Oracle(ofd.Params(nx=16, qx_half=4, qy=4, qz=0, kn=0.1, eta0=0.2, accel_y=0.05))
+    p.step(100)
+    M = p.moments()
+    np.testing.assert_allclose(M["uy"], M["uy"][::-1], rtol=1e-12, atol=1e-15)
+    a = ofd.Oracle(ofd.Params(nx=16, qx_half=4, qy=0, qz=0, kn=0.1, eta0=0.2, T_left=0.9, T_right=1.1))
+    b = ofd.Oracle(ofd.Params(nx=16, qx_half=4, qy=0, qz=0, kn=0.1, eta0=0.2, T_left=1.1, T_right=0.9))
+    a.step(100)
+    b.step(100)
+    Ma, Mb = a.moments(), b.moments()
+    np.testing.assert_allclose(Ma["T"], Mb["T"][::-1], rtol=1e-13)
+    np.testing.assert_allclose(Ma["qx"], -Mb["qx"][::-1], rtol=1e-11, atol=1e-15)
+
+
+def test_reduced_and_unreduced_evolution_agree():
+    """The (phi, theta) targets are exactly the z-moments of the unreduced ones (pinned in
+    test_oracle_collision); the evolutions differ only because WENO's weights are nonlinear
+    (sum_kz WENO(f_kz) != WENO(sum_kz f_kz)), i.e. at truncation level: the difference is
+    small and shrinks under grid refinement."""
+    def diff(nx):
+        kw = dict(nx=nx, qx_half=4, kn=0.1, eta0=0.2, U_left=-0.3, U_right=0.3, T_left=0.95, T_right=1.05, cfl=0.5)
+        u = ofd.Oracle(ofd.Params(qy=4, qz=4, **kw))
+        r = ofd.Oracle(ofd.Params(qy=4, qz=0, **kw))
+        nsteps = int(round(0.15 / u.dt))
+        u.step(nsteps)
+        r.step(nsteps)
+        Mu, Mr = u.moments(), r.moments()
+        return max(np.abs(Mu[k] - Mr[k]).max() for k in ("n", "uy", "T"))
+    d12, d24 = diff(12), diff(24)
+    assert d12 < 2e-4 and d24 < 0.7 * d12, (d12, d24)
+
+
+def test_force_momentum_source():
+    """-a_y (K f): at the uniform resting equilibrium only the force acts, and
+    sum_k p_y L_k = a_y n at every node (integration by parts, App. A)."""
+    o = ofd.Oracle(ofd.Params(nx=10, qx_half=4, qy=6, qz=0, kn=0.1, eta0=0.1, accel_y=0.07))
+    L = o.L(o.f)
+    src = np.sum(o.mt[None, :, None] * o.py[None, :, None] * L, axis=(0, 1))
+    np.testing.assert_allclose(src, 0.07 * o.moments()["n"], rtol=1e-13)
+    np.testing.assert_allclose(np.sum(o.mt[None, :, None] * L, axis=(0, 1)), 0.0, atol=1e-14)
+
+
+def test_free_molecular_fourier():
+    """eta0 = 0, Kn -> inf: n = 1 and q_x = 4/sqrt(2 pi) sqrt(T_L T_R)/(sqrt T_L + sqrt T_R) (T_L - T_R)
+    (half-range Maxwellians emitted by the two walls, zero net mass flux); exact for Q_x^h >= 4."""
+    TL, TR = 0.9, 1.1
+    o = ofd.Oracle(ofd.Params(nx=8, qx_half=4, qy=0, qz=0, kn=1e12, eta0=0.0, T_left=TL, T_right=TR, cfl=1.0))
+    o.step(2400)
+    M = o.moments()
+    qex = 4 / math.sqrt(2 * math.pi) * math.sqrt(TL * TR) / (math.sqrt(TL) + math.sqrt(TR)) * (TL - TR)
+    assert np.abs(M["qx"] / qex - 1).max() < 1e-10
+    assert np.abs(M["n"] - 1).max() < 1e-10
+
+
+def test_free_molecular_couette():
+    """eta0 = 0, Kn -> inf, equal wall temperatures: Pi_xy = -sqrt(T_w/(2 pi)) (U_R - U_L), u_y = 0."""
+    UL, UR = -0.3, 0.42
+    o = ofd.Oracle(ofd.Params(nx=8, qx_half=4, qy=4, qz=0, kn=1e12, eta0=0.0, U_left=UL, U_right=UR, cfl=1.0))
+    o.step(1200)
+    M = o.moments()
+    pex = -math.sqrt(1 / (2 * math.pi)) * (UR - UL)
+    assert np.abs(M["Pxy"] / pex - 1).max() < 1e-10
+    np.testing.assert_allclose(M["uy"], 0.5 * (UL + UR), atol=1e-10)
