@@ -1,0 +1,167 @@
+/*
+ * fdlb.h -- C ABI of the GB300 FDLB solver for the simplified Enskog equation
+ * (Busuioc & Sofonea, "Bounded flows of dense gases", arXiv 2308.15407).
+ *
+ * What one call computes: the per-time-step update of the discrete reduced
+ * (or unreduced) distribution f(x_i, p_kappa) of Eqs. (evolution_1D) and
+ * (evolution_2D) -- moments (Eq. macro_LB), the Carnahan-Starling contact
+ * value (Eq. chi), the Shakhov relaxation (Eq. j0), the first-order Enskog
+ * correction J1 (Eq. j1), WENO-5 advection (Sec. III B 2) with diffuse-
+ * reflection walls (Sec. III B) and the force term (App. A, Eq. kernel_H),
+ * all inside the TVD Runge-Kutta scheme (Eq. rk3) -- for a batch of
+ * independent wall-bounded 1D channel problems (Fourier, Couette, Poiseuille
+ * flow, Sec. IV).
+ *
+ * Conventions
+ *  - Units: m = k_B = T_ref = 1, channel width D = 1 (walls at x = -1/2 and
+ *    x = +1/2), mean number density 1.  Kn refers to the channel width:
+ *    mu0(T) = (5/16) sqrt(2 pi) chi(eta0) Kn sqrt(T).
+ *  - Every call returns an int: FDLB_OK (0) or a negative FDLB_E* code; no
+ *    C++ exception crosses the ABI.  fdlb_last_error() gives a message.
+ *  - Ownership: the caller owns the device workspace (any device allocation,
+ *    e.g. a torch uint8 tensor of fdlb_workspace_bytes() bytes, 256-byte
+ *    aligned) and every host buffer.  The context owns only a small host-side
+ *    record; fdlb_destroy() frees it and never touches the workspace.
+ *  - Streams: all device work is enqueued on the cudaStream_t passed to
+ *    fdlb_create (as void*; NULL = legacy default stream).  fdlb_step is
+ *    asynchronous; every call that returns host data synchronises that stream.
+ *  - Layout of f in the workspace: per instance, f[kappa][node] (node index
+ *    contiguous, row stride rounded up to 32), kappa = kx * T_c + t with
+ *    kx = 0..Q-1 for +p_k and Q..2Q-1 for -p_k (half-range nodes, Eq. hh_pk),
+ *    t the transverse index: t = ky*Q_z + kz (unreduced), t = 2 ky + slot
+ *    (2D reduced, slot 0 = phi, 1 = theta), t = slot (1D reduced).
+ */
+#ifndef FDLB_H
+#define FDLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDLB_ABI_VERSION 1
+
+/* Return codes. */
+#define FDLB_OK            0
+#define FDLB_EINVAL       -1   /* invalid argument or parameter set */
+#define FDLB_ENOMEM       -2   /* workspace too small or misaligned */
+#define FDLB_ECUDA        -3   /* a CUDA runtime call failed (message in fdlb_last_error) */
+#define FDLB_ENONFINITE   -4   /* an instance produced a non-finite moment */
+#define FDLB_EUNPHYSICAL  -5   /* an instance produced n <= 0 or T <= 0 */
+#define FDLB_ETIMEOUT     -6   /* fdlb_run hit its wall-clock limit */
+#define FDLB_ESTATE       -7   /* state buffer does not match this context */
+
+/* Flow types (Sec. IV): informational; the physics is set by the walls and the force. */
+#define FDLB_FOURIER      0
+#define FDLB_COUETTE      1
+#define FDLB_POISEUILLE   2
+
+/* Grid mapping x(s), s in (-1, 1), cell-centred nodes s_i = -1 + (i + 1/2) 2/nx. */
+#define FDLB_GRID_UNIFORM 0    /* x = s/2 */
+#define FDLB_GRID_TANH    1    /* x = tanh(A s)/(2 tanh A), A = stretch (nodes crowd at the walls) */
+
+/* Storage precision of f. */
+#define FDLB_FP64          0   /* everything in FP64 */
+#define FDLB_FP32_STORAGE  1   /* f stored, advected and combined in FP32; moments, gradients,
+                                  projections and the residual in FP64 */
+
+/* Per-instance status (fdlb_status). */
+#define FDLB_ACTIVE        0
+#define FDLB_CONVERGED     1
+#define FDLB_FAILED_NONFINITE  2
+#define FDLB_FAILED_UNPHYSICAL 3
+
+/* Parameters of one channel problem.  Set struct_size = sizeof(fdlb_params). */
+typedef struct fdlb_params {
+    uint32_t struct_size;
+    int32_t  flow;        /* FDLB_FOURIER | FDLB_COUETTE | FDLB_POISEUILLE */
+    int32_t  nx;          /* grid nodes, 8 <= nx <= 4096 */
+    int32_t  grid;        /* FDLB_GRID_UNIFORM | FDLB_GRID_TANH */
+    int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..16 (2*qx_half x-velocities) */
+    int32_t  qy;          /* full-range order on y, 0 or 2..8; 0 = 1D reduced (p_y integrated out) */
+    int32_t  qz;          /* full-range order on z, 0 or 3..8; 0 = (phi, theta) reduced slots */
+    int32_t  precision;   /* FDLB_FP64 | FDLB_FP32_STORAGE */
+    int32_t  j1_shear;    /* 0: J1 as printed for 2D flows; 1: add the 2 zeta_x zeta_y d_x u_y term of Eq. (j1) */
+    int32_t  reserved;    /* must be 0 */
+    double   stretch;     /* A of FDLB_GRID_TANH (> 0) */
+    double   kn;          /* Knudsen number referred to the channel width (> 0) */
+    double   eta0;        /* mean reduced density eta0 = b n0/4, 0 <= eta0 < 0.5 */
+    double   T_left, T_right;   /* wall temperatures (> 0) */
+    double   U_left, U_right;   /* wall velocities along y */
+    double   accel_y;     /* body-force acceleration along y (Poiseuille) */
+    double   cfl;         /* dt = cfl * min_i dx_i / max_k p_k when dt == 0 */
+    double   dt;          /* explicit time step, or 0 */
+    double   T_init;      /* initial uniform temperature, or 0 for the mean wall temperature */
+} fdlb_params;
+
+typedef struct fdlb_ctx fdlb_ctx;
+
+/* ABI version of the loaded library (FDLB_ABI_VERSION). */
+int32_t fdlb_abi_version(void);
+
+/* Message for the last error on ctx (or the last context-free error when ctx == NULL).
+ * The string is owned by the library and valid until the next call on ctx. */
+const char* fdlb_last_error(const fdlb_ctx* ctx);
+
+/* Device workspace needed by a batch of `count` instances described by params[0..count-1].
+ * Returns 0 for an invalid parameter set (fdlb_last_error(NULL) says why). */
+size_t fdlb_workspace_bytes(const fdlb_params* params, int32_t count);
+
+/* Build the quadratures, grids and tables of every instance, place them and the state in
+ * dev_workspace (ws_bytes >= fdlb_workspace_bytes, 256-byte aligned device memory), and
+ * enqueue the initial uniform projected equilibrium (n = 1, u = 0, T = T_init) on `stream`.
+ * *out receives the context.  Errors: FDLB_EINVAL, FDLB_ENOMEM, FDLB_ECUDA. */
+int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t count,
+                void* dev_workspace, size_t ws_bytes, void* stream);
+
+/* Release the host record.  The workspace stays owned by the caller. */
+void fdlb_destroy(fdlb_ctx* ctx);
+
+/* Number of instances, nodes of instance i, velocities of instance i. */
+int fdlb_info(const fdlb_ctx* ctx, int32_t inst, int32_t* nx, int32_t* nvel, double* dt);
+
+/* Advance every ACTIVE instance by nsteps RK3 steps (asynchronous).  Each step computes the
+ * per-step residual of every instance (change of n, T, u_x, u_y in the cell-width-weighted
+ * L2 norm; relative for n and T) and marks non-finite or unphysical instances FAILED.
+ * With freeze_tol > 0 an instance whose residual falls below freeze_tol is marked CONVERGED
+ * and is not advanced further.  Errors: FDLB_EINVAL, FDLB_ECUDA. */
+int fdlb_step(fdlb_ctx* ctx, int64_t nsteps, double freeze_tol);
+
+/* Steady-state solve: step in chunks of check_every steps until every instance is CONVERGED
+ * (residual < tol) or FAILED, or max_steps steps were taken, or timeout_s seconds of wall
+ * time passed (FDLB_ETIMEOUT).  On stopping it returns FDLB_ENONFINITE or FDLB_EUNPHYSICAL
+ * when some instance failed (the others are still advanced until they stop), else FDLB_OK
+ * when all converged, or 1 when max_steps was reached with instances still active. */
+int fdlb_run(fdlb_ctx* ctx, double tol, int64_t max_steps, int64_t check_every, double timeout_s);
+
+/* Host copy of the moments of instance `inst` (synchronises the stream):
+ * host_out[8 * nx] = rows n, u_x, u_y, T, q_x, q_y, Pi_xx, Pi_xy (kinetic, Eq. macro_LB). */
+int fdlb_moments(fdlb_ctx* ctx, int32_t inst, double* host_out);
+
+/* Per-instance last residual, status and step count (synchronises).  Any pointer may be NULL. */
+int fdlb_status(fdlb_ctx* ctx, double* residual, int32_t* status, int64_t* steps);
+
+/* Reset instance `inst` to the projected local equilibrium with the given profiles
+ * (u_x = 0; host arrays of nx values; n > 0, T > 0) and mark it ACTIVE with 0 steps. */
+int fdlb_set_profiles(fdlb_ctx* ctx, int32_t inst, const double* n, const double* uy, const double* T);
+
+/* Checkpoint of instance `inst`: f, step count and a parameter hash.  fdlb_state_bytes gives
+ * the size; get copies device -> host (synchronises), set copies host -> device (FDLB_ESTATE
+ * when the buffer belongs to other parameters). */
+size_t fdlb_state_bytes(const fdlb_ctx* ctx, int32_t inst);
+int fdlb_get_state(fdlb_ctx* ctx, int32_t inst, void* host, size_t bytes);
+int fdlb_set_state(fdlb_ctx* ctx, int32_t inst, const void* host, size_t bytes);
+
+/* Host-only: the library's own Gauss rules (for checking the tables; no GPU needed).
+ * kind 0 = half-range Gauss-Hermite on [0, inf) (Sec. III A 2), kind 1 = full-range (App. A);
+ * weights are normalised to the weight omega(p) = exp(-p^2/2)/sqrt(2 pi).  nodes/weights
+ * receive q values.  Errors: FDLB_EINVAL. */
+int fdlb_quadrature(int32_t kind, int32_t q, double* nodes, double* weights);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDLB_H */

@@ -1,0 +1,709 @@
+// Host set-up and C ABI of the FDLB solver (see include/fdlb.h).
+//
+// Everything here is built from the paper's definitions, independently of any
+// other implementation:
+//  * Gauss rules (Sec. III A 2 half-range, App. A full-range): recurrence
+//    coefficients of the orthonormal polynomials by the Stieltjes procedure on a
+//    discretised weight (composite Gauss-Legendre), nodes as eigenvalues of the
+//    Jacobi matrix (Sturm-sequence bisection, Newton polish), Christoffel weights.
+//  * 6th-order gradient stencils (Sec. III B 3) with one-sided / biased 7-point
+//    stencils at the 3 nodes next to a wall (solved from the moment conditions).
+//  * Grid mapping, time step, workspace layout, work lists, error handling.
+#include "fdlb_internal.h"
+#include "fdlb_launch.h"
+#include "../../include/fdlb.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fdlb;
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+struct fdlb_ctx {
+    int count = 0;
+    std::vector<fdlb_params> prm;
+    std::vector<Inst> inst;           // host copies (device pointers inside)
+    Inst* d_inst = nullptr;
+    Work* d_mom = nullptr;
+    Work* d_upd = nullptr;
+    int n_mom = 0, n_upd = 0;
+    int* d_status_all = nullptr;      // count ints (Inst::status points here)
+    long long* d_steps_all = nullptr;
+    double* d_resid_all = nullptr;    // count doubles (misc[M_RESID] copies)
+    cudaStream_t stream = nullptr;
+    size_t smem_upd_f64 = 0, smem_upd_f32 = 0;
+    bool any_fp32 = false, any_fp64 = false;
+    std::string err;
+};
+
+static int fail(fdlb_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    g_err = msg;
+    return code;
+}
+
+static int cuda_check(fdlb_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return FDLB_OK;
+    return fail(c, FDLB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" int32_t fdlb_abi_version(void) { return FDLB_ABI_VERSION; }
+
+extern "C" const char* fdlb_last_error(const fdlb_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// quadrature
+// ---------------------------------------------------------------------------
+namespace {
+
+// Gauss-Legendre rule on [-1, 1] (Newton on the Legendre three-term recurrence).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs((double)dz) < 1e-19) break;
+        }
+        x[i] = (double)z;
+        w[i] = (double)(2 / ((1 - z * z) * dp * dp));
+    }
+}
+
+// Monic recurrence pi_{l+1} = (p - alpha_l) pi_l - beta_l pi_{l-1}, l = 0..L-1, for the
+// half-range weight omega(p) = exp(-p^2/2)/sqrt(2 pi) on [0, inf), by the Stieltjes
+// procedure on the discrete measure of a composite Gauss-Legendre rule on [0, 20]
+// (the weight below 1e-86 beyond); beta_0 = mass = 1/2.
+void half_range_recurrence(int L, std::vector<double>& alpha, std::vector<double>& beta) {
+    std::vector<double> gx, gw;
+    const int npt = 24, panels = 80;
+    gauss_legendre(npt, gx, gw);
+    const double hi = 20.0, h = hi / panels;
+    std::vector<double> t, W;
+    for (int pnl = 0; pnl < panels; ++pnl)
+        for (int j = 0; j < npt; ++j) {
+            double x = (pnl + 0.5) * h + 0.5 * h * gx[j];
+            t.push_back(x);
+            W.push_back(0.5 * h * gw[j] * std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI));
+        }
+    const size_t P = t.size();
+    std::vector<double> pm(P, 0.0), pc(P, 1.0), pn(P);
+    alpha.assign(L, 0.0);
+    beta.assign(L, 0.0);
+    double norm_prev = 1.0;
+    for (int l = 0; l < L; ++l) {
+        double nrm = 0, xn = 0;
+        for (size_t j = 0; j < P; ++j) {
+            nrm += W[j] * pc[j] * pc[j];
+            xn += W[j] * t[j] * pc[j] * pc[j];
+        }
+        alpha[l] = (double)(xn / nrm);
+        beta[l] = (double)(l == 0 ? nrm : nrm / norm_prev);
+        for (size_t j = 0; j < P; ++j) pn[j] = (t[j] - (double)alpha[l]) * pc[j] - (double)beta[l] * pm[j];
+        pm.swap(pc);
+        pc.swap(pn);
+        norm_prev = nrm;
+    }
+}
+
+struct Rule {
+    std::vector<double> x, w;     // nodes (ascending), weights
+    std::vector<double> alpha;    // alpha_l, l < Q+1
+    std::vector<double> beta;     // beta_l (beta_0 = total mass), l < Q+1
+};
+
+// Eigenvalues of the symmetric tridiagonal Jacobi matrix (diag alpha, off-diagonal
+// sqrt(beta_l), l = 1..Q-1) by Sturm-count bisection, polished by Newton on pi_Q.
+void jacobi_nodes(int Q, const std::vector<double>& alpha, const std::vector<double>& beta, std::vector<double>& x) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < Q; ++i) {
+        double r = (i > 0 ? std::sqrt(beta[i]) : 0.0) + (i + 1 < Q ? std::sqrt(beta[i + 1]) : 0.0);
+        lo = std::min(lo, alpha[i] - r);
+        hi = std::max(hi, alpha[i] + r);
+    }
+    auto count_below = [&](double s) {
+        int cnt = 0;
+        double d = 1.0;
+        for (int i = 0; i < Q; ++i) {
+            d = (alpha[i] - s) - (i > 0 ? beta[i] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0) ++cnt;
+        }
+        return cnt;
+    };
+    x.assign(Q, 0.0);
+    for (int k = 0; k < Q; ++k) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 200 && b - a > 1e-15 * std::max(1.0, std::fabs(a)); ++it) {
+            double m = 0.5 * (a + b);
+            if (count_below(m) > k) b = m; else a = m;
+        }
+        double z = 0.5 * (a + b);
+        for (int it = 0; it < 5; ++it) {      // Newton on the monic pi_Q
+            double p0 = 1, p1 = z - alpha[0], d0 = 0, d1 = 1;
+            for (int l = 1; l < Q; ++l) {
+                double p2 = (z - alpha[l]) * p1 - beta[l] * p0;
+                double d2 = p1 + (z - alpha[l]) * d1 - beta[l] * d0;
+                p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+            }
+            if (Q == 1) { p1 = z - alpha[0]; d1 = 1; }
+            if (d1 == 0) break;
+            z -= p1 / d1;
+        }
+        x[k] = (double)z;
+    }
+}
+
+// Orthonormal polynomial values h_0..h_{L-1} at x from the monic recurrence.
+void ortho_values(int L, const std::vector<double>& alpha, const std::vector<double>& beta, double x,
+                  std::vector<double>& h) {
+    h.assign(L, 0.0);
+    double hm = 0.0, hc = 1.0 / std::sqrt((double)beta[0]);
+    for (int l = 0; l < L; ++l) {
+        h[l] = hc;
+        if (l + 1 < L) {
+            double bn = std::sqrt((double)beta[l + 1]);
+            double b = l > 0 ? std::sqrt((double)beta[l]) : 0.0;
+            double hn = ((x - alpha[l]) * hc - b * hm) / bn;
+            hm = hc;
+            hc = hn;
+        }
+    }
+}
+
+Rule make_rule(int kind, int Q) {
+    Rule r;
+    if (kind == 0) {
+        half_range_recurrence(Q + 1, r.alpha, r.beta);
+    } else {
+        r.alpha.assign(Q + 1, 0.0);
+        r.beta.resize(Q + 1);
+        r.beta[0] = 1.0;
+        for (int l = 1; l <= Q; ++l) r.beta[l] = l;     // He_{l+1} = p He_l - l He_{l-1}
+    }
+    jacobi_nodes(Q, r.alpha, r.beta, r.x);
+    r.w.resize(Q);
+    std::vector<double> h;
+    for (int k = 0; k < Q; ++k) {
+        ortho_values(Q, r.alpha, r.beta, r.x[k], h);
+        double s = 0;
+        for (int l = 0; l < Q; ++l) s += h[l] * h[l];
+        r.w[k] = (double)(1.0 / s);
+    }
+    return r;
+}
+
+// Weights c_j, j = 0..6, with sum_j c_j F(j) = F'(x0) for polynomials of degree <= 6:
+// c_j = l_j'(x0) for the Lagrange basis on the integer nodes 0..6.  Every product below is
+// an exact integer in double arithmetic; each term is rounded once.
+void stencil7(int x0, double* c) {
+    for (int j = 0; j < 7; ++j) {
+        double den = 1.0;
+        for (int l = 0; l < 7; ++l)
+            if (l != j) den *= (double)(j - l);
+        double num = 0.0;
+        for (int m = 0; m < 7; ++m) {
+            if (m == j) continue;
+            double prod = 1.0;
+            for (int l = 0; l < 7; ++l)
+                if (l != j && l != m) prod *= (double)(x0 - l);
+            num += prod;
+        }
+        c[j] = num / den;
+    }
+}
+
+double chi_cs(double eta) { return (2.0 - eta) / (2.0 * (1.0 - eta) * (1.0 - eta) * (1.0 - eta)); }
+
+int validate(const fdlb_params& p, std::string& why) {
+    auto bad = [&](const char* m) { why = m; return FDLB_EINVAL; };
+    if (p.struct_size != sizeof(fdlb_params)) return bad("struct_size != sizeof(fdlb_params)");
+    if (p.nx < 8 || p.nx > 4096) return bad("nx must be in [8, 4096]");
+    if (p.qx_half < 1 || p.qx_half > QMAX) return bad("qx_half must be in [1, 16]");
+    if (p.qy != 0 && (p.qy < 2 || p.qy > QYMAX)) return bad("qy must be 0 or in [2, 8]");
+    if (p.qz != 0 && (p.qz < 3 || p.qz > QZMAX)) return bad("qz must be 0 or in [3, 8]");
+    if (p.qy == 0 && p.qz != 0) return bad("qy == 0 (1D reduced) requires qz == 0");
+    if (p.qy == 0 && (p.U_left != 0 || p.U_right != 0 || p.accel_y != 0))
+        return bad("the 1D reduced form (qy == 0) has no y motion: walls at rest, no force");
+    if (p.grid != FDLB_GRID_UNIFORM && p.grid != FDLB_GRID_TANH) return bad("unknown grid");
+    if (p.grid == FDLB_GRID_TANH && !(p.stretch > 0)) return bad("stretch must be > 0");
+    if (p.precision != FDLB_FP64 && p.precision != FDLB_FP32_STORAGE) return bad("unknown precision");
+    if (p.j1_shear != 0 && p.j1_shear != 1) return bad("j1_shear must be 0 or 1");
+    if (p.reserved != 0) return bad("reserved must be 0");
+    if (!(p.kn > 0) || !std::isfinite(p.kn)) return bad("kn must be > 0");
+    if (!(p.eta0 >= 0 && p.eta0 < 0.5)) return bad("eta0 must be in [0, 0.5)");
+    if (!(p.T_left > 0) || !(p.T_right > 0)) return bad("wall temperatures must be > 0");
+    if (!std::isfinite(p.U_left) || !std::isfinite(p.U_right) || !std::isfinite(p.accel_y)) return bad("non-finite wall speed or force");
+    if (!(p.dt >= 0) || (p.dt == 0 && !(p.cfl > 0))) return bad("need dt > 0 or cfl > 0");
+    if (!(p.T_init >= 0)) return bad("T_init must be >= 0");
+    return FDLB_OK;
+}
+
+// Byte layout of one instance inside the workspace.
+struct Layout {
+    size_t tables = 0, fbuf = 0, node = 0, tab = 0, misc = 0, total = 0;
+    int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0;
+};
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+Layout layout_of(const fdlb_params& p) {
+    Layout L;
+    L.form = p.qz > 0 ? FORM_UNREDUCED : (p.qy > 0 ? FORM_REDUCED2D : FORM_REDUCED1D);
+    L.Tc = L.form == FORM_UNREDUCED ? p.qy * p.qz : (L.form == FORM_REDUCED2D ? 2 * p.qy : 2);
+    L.K = 2 * p.qx_half * L.Tc;
+    L.ld = (p.nx + TILE - 1) / TILE * TILE;
+    L.ntab = 8 * p.qx_half + 4 * L.Tc + 1;
+    L.My = p.qy > 0 ? (p.qy + 5) / 2 : 0;     // 2 My - 1 >= qy + 2
+    L.Mz = p.qz > 0 ? (p.qz + 5) / 2 : 0;
+    const int Q = p.qx_half;
+    size_t nd = 0;
+    // tables (doubles), each padded to 256 B
+    auto add = [&](size_t n) { nd += al256(n * 8) / 8; };
+    add(2 * Q); add(MX); add(MX); add(Q); add(Q + 1); add(Q + 1); add(Q * Q);
+    add(QYMAX); add(MYMAX); add(MYMAX); add(QYMAX * QYMAX);
+    add(QZMAX); add(MYMAX); add(MYMAX); add(QZMAX * QZMAX);
+    add(QYMAX * QYMAX);
+    add(L.Tc); add(L.Tc); add(L.Tc);
+    add(p.nx); add(p.nx); add(21);
+    add(L.K); add(L.K);
+    add(QYMAX + 2); add(QYMAX + 2);
+    L.tables = nd * 8;
+    const size_t es = p.precision == FDLB_FP64 ? 8 : 4;
+    L.fbuf = al256((size_t)L.K * L.ld * es);
+    L.node = al256((size_t)NROWS * L.ld * 8);
+    L.tab = al256((size_t)L.ntab * L.ld * 8);
+    L.misc = al256(8 * 8);
+    L.total = L.tables + 3 * L.fbuf + L.node + L.tab + L.misc;
+    return L;
+}
+
+size_t global_bytes(int count, int n_mom, int n_upd) {
+    return al256(sizeof(Inst) * count) + al256(sizeof(Work) * n_mom) + al256(sizeof(Work) * n_upd) +
+           al256(sizeof(int) * count) + al256(sizeof(long long) * count) + al256(sizeof(double) * count);
+}
+
+const int KC = 32;   // velocities per update work item
+
+void count_work(const std::vector<fdlb_params>& p, int& n_mom, int& n_upd) {
+    n_mom = n_upd = 0;
+    for (auto& q : p) {
+        Layout L = layout_of(q);
+        int tiles = (q.nx + TILE - 1) / TILE;
+        n_mom += tiles;
+        n_upd += tiles * ((L.K + KC - 1) / KC);
+    }
+}
+
+}  // namespace
+
+extern "C" int fdlb_quadrature(int32_t kind, int32_t q, double* nodes, double* weights) {
+    if ((kind != 0 && kind != 1) || q < 1 || q > 64 || !nodes || !weights) return fail(nullptr, FDLB_EINVAL, "fdlb_quadrature: bad arguments");
+    Rule r = make_rule(kind, q);
+    for (int k = 0; k < q; ++k) { nodes[k] = r.x[k]; weights[k] = r.w[k]; }
+    return FDLB_OK;
+}
+
+extern "C" size_t fdlb_workspace_bytes(const fdlb_params* params, int32_t count) {
+    if (!params || count < 1) { g_err = "fdlb_workspace_bytes: need params and count >= 1"; return 0; }
+    std::vector<fdlb_params> p(params, params + count);
+    for (int i = 0; i < count; ++i) {
+        std::string why;
+        if (validate(p[i], why) != FDLB_OK) { g_err = "instance " + std::to_string(i) + ": " + why; return 0; }
+    }
+    int n_mom, n_upd;
+    count_work(p, n_mom, n_upd);
+    size_t tot = global_bytes(count, n_mom, n_upd);
+    for (auto& q : p) tot += layout_of(q).total;
+    return tot;
+}
+
+extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t count, void* dev_workspace,
+                           size_t ws_bytes, void* stream) {
+    if (!out || !params || count < 1) return fail(nullptr, FDLB_EINVAL, "fdlb_create: bad arguments");
+    *out = nullptr;
+    size_t need = fdlb_workspace_bytes(params, count);
+    if (need == 0) return fail(nullptr, FDLB_EINVAL, g_err);
+    if (!dev_workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(dev_workspace) & 255))
+        return fail(nullptr, FDLB_ENOMEM, "fdlb_create: workspace missing, smaller than fdlb_workspace_bytes, or not 256-byte aligned");
+    fdlb_ctx* c = new fdlb_ctx();
+    c->count = count;
+    c->prm.assign(params, params + count);
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+
+    int n_mom, n_upd;
+    count_work(c->prm, n_mom, n_upd);
+    c->n_mom = n_mom;
+    c->n_upd = n_upd;
+    char* base = reinterpret_cast<char*>(dev_workspace);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base + off; off += al256(bytes); return p; };
+    c->d_inst = reinterpret_cast<Inst*>(take(sizeof(Inst) * count));
+    c->d_mom = reinterpret_cast<Work*>(take(sizeof(Work) * n_mom));
+    c->d_upd = reinterpret_cast<Work*>(take(sizeof(Work) * n_upd));
+    c->d_status_all = reinterpret_cast<int*>(take(sizeof(int) * count));
+    c->d_steps_all = reinterpret_cast<long long*>(take(sizeof(long long) * count));
+    c->d_resid_all = reinterpret_cast<double*>(take(sizeof(double) * count));
+
+    std::vector<Work> wm, wu;
+    std::vector<char> staging;        // host image of all table regions
+    std::vector<std::pair<size_t, size_t>> regions;   // (offset, size) of table regions
+    size_t max_smem64 = 0, max_smem32 = 0;
+
+    for (int ii = 0; ii < count; ++ii) {
+        const fdlb_params& p = c->prm[ii];
+        Layout L = layout_of(p);
+        const int Q = p.qx_half, N = p.nx;
+        Inst I;
+        std::memset(&I, 0, sizeof(I));
+        I.N = N; I.ld = L.ld; I.Q = Q; I.Qy = p.qy; I.Qz = p.qz; I.form = L.form; I.Tc = L.Tc; I.K = L.K;
+        I.Mx = MX; I.My = L.My; I.Mz = L.Mz;
+        I.precision = p.precision; I.j1_shear = p.j1_shear; I.ntab = L.ntab;
+        I.kn = p.kn; I.eta0 = p.eta0; I.chi0 = chi_cs(p.eta0);
+        I.mu0c = (5.0 / 16.0) * std::sqrt(2.0 * M_PI) * I.chi0 * p.kn;
+        I.accel_y = p.accel_y;
+        I.T_L = p.T_left; I.T_R = p.T_right; I.U_L = p.U_left; I.U_R = p.U_right;
+        I.T_init = p.T_init > 0 ? p.T_init : 0.5 * (p.T_left + p.T_right);
+        I.ds = 2.0 / N;
+
+        // ---- host tables
+        size_t tab_off = off;
+        std::vector<double> img(L.tables / 8, 0.0);
+        size_t pos = 0;
+        auto put = [&](const double** dst, size_t n) -> double* {
+            double* h = img.data() + pos;
+            *dst = reinterpret_cast<const double*>(base + tab_off + pos * 8);
+            pos += al256(n * 8) / 8;
+            return h;
+        };
+        auto putw = [&](double** dst, size_t n) -> double* {
+            double* h = img.data() + pos;
+            *dst = reinterpret_cast<double*>(base + tab_off + pos * 8);
+            pos += al256(n * 8) / 8;
+            return h;
+        };
+        Rule xr = make_rule(0, Q);
+        Rule xa = make_rule(0, MX);
+        {
+            double* h = put(&I.px, 2 * Q);
+            for (int k = 0; k < Q; ++k) { h[k] = xr.x[k]; h[Q + k] = -xr.x[k]; }
+            h = put(&I.xq, MX); for (int m = 0; m < MX; ++m) h[m] = xa.x[m];
+            h = put(&I.xw, MX); for (int m = 0; m < MX; ++m) h[m] = xa.w[m];
+            h = put(&I.xa, Q); for (int l = 0; l < Q; ++l) h[l] = xr.alpha[l];
+            double* hb = put(&I.xb, Q + 1);
+            double* hib = put(&I.xib, Q + 1);
+            for (int l = 0; l <= Q; ++l) {
+                hb[l] = l ? std::sqrt(xr.beta[l]) : 0.0;
+                hib[l] = l ? 1.0 / std::sqrt(xr.beta[l]) : 0.0;
+            }
+            I.x_h0 = 1.0 / std::sqrt(xr.beta[0]);
+            h = put(&I.xH, Q * Q);
+            std::vector<double> hv;
+            for (int k = 0; k < Q; ++k) {
+                ortho_values(Q, xr.alpha, xr.beta, xr.x[k], hv);
+                for (int l = 0; l < Q; ++l) h[l * Q + k] = (double)(xr.w[k] * hv[l]);
+            }
+        }
+        auto full_tables = [&](int Qn, int M, const double** nn, const double** aq, const double** aw, const double** H) {
+            double* hn = put(nn, QYMAX);
+            double* hq = put(aq, MYMAX);
+            double* hw = put(aw, MYMAX);
+            double* hH = put(H, QYMAX * QYMAX);
+            if (Qn == 0) return;
+            Rule r = make_rule(1, Qn), a = make_rule(1, M);
+            for (int k = 0; k < Qn; ++k) hn[k] = r.x[k];
+            for (int m = 0; m < M; ++m) { hq[m] = a.x[m]; hw[m] = a.w[m]; }
+            std::vector<double> hv;
+            for (int k = 0; k < Qn; ++k) {
+                ortho_values(Qn, r.alpha, r.beta, r.x[k], hv);
+                for (int l = 0; l < Qn; ++l) hH[l * Qn + k] = (double)(r.w[k] * hv[l]);
+            }
+        };
+        full_tables(p.qy, L.My, &I.yn, &I.yq, &I.yw, &I.yH);
+        full_tables(p.qz, L.Mz, &I.zn, &I.zq, &I.zw, &I.zH);
+        {
+            // momentum-derivative kernel on y (App. A, Eq. kernel_H):
+            // K[k][k'] = -w_k sum_{l=0}^{Q-2} He_{l+1}(p_k) He_l(p_k')/l!
+            double* h = put(&I.Ky, QYMAX * QYMAX);
+            if (p.qy > 0) {
+                Rule r = make_rule(1, p.qy);
+                const int Qy = p.qy;
+                std::vector<std::vector<double>> He(Qy + 1, std::vector<double>(Qy));
+                for (int k = 0; k < Qy; ++k) {
+                    He[0][k] = 1;
+                    He[1][k] = r.x[k];
+                    for (int l = 1; l < Qy; ++l) He[l + 1][k] = r.x[k] * He[l][k] - l * He[l - 1][k];
+                }
+                for (int k = 0; k < Qy; ++k)
+                    for (int kp = 0; kp < Qy; ++kp) {
+                        double s = 0, fact = 1;
+                        for (int l = 0; l <= Qy - 2; ++l) {
+                            if (l > 0) fact *= l;
+                            s += He[l + 1][k] * He[l][kp] / fact;
+                        }
+                        h[k * Qy + kp] = (double)(-r.w[k] * s);
+                    }
+            }
+        }
+        {
+            double* hm = put(&I.tmt, L.Tc);
+            double* hy = put(&I.tpy, L.Tc);
+            double* he = put(&I.tet, L.Tc);
+            if (L.form == FORM_UNREDUCED) {
+                Rule ry = make_rule(1, p.qy), rz = make_rule(1, p.qz);
+                for (int ky = 0; ky < p.qy; ++ky)
+                    for (int kz = 0; kz < p.qz; ++kz) {
+                        int t = ky * p.qz + kz;
+                        hm[t] = 1.0; hy[t] = ry.x[ky]; he[t] = 0.5 * rz.x[kz] * rz.x[kz];
+                    }
+            } else if (L.form == FORM_REDUCED2D) {
+                Rule ry = make_rule(1, p.qy);
+                for (int ky = 0; ky < p.qy; ++ky) {
+                    hm[2 * ky] = 1.0; hy[2 * ky] = ry.x[ky]; he[2 * ky] = 0.0;
+                    hm[2 * ky + 1] = 0.0; hy[2 * ky + 1] = ry.x[ky]; he[2 * ky + 1] = 0.5;
+                }
+            } else {
+                hm[0] = 1.0; hy[0] = 0.0; he[0] = 0.0;
+                hm[1] = 0.0; hy[1] = 0.0; he[1] = 0.5;
+            }
+        }
+        {
+            double* hxi = put(&I.xpinv, N);
+            double* hdx = put(&I.dxw, N);
+            double xpmin = 1e300;
+            for (int i = 0; i < N; ++i) {
+                double s = -1.0 + (i + 0.5) * I.ds, xp;
+                if (p.grid == FDLB_GRID_UNIFORM) xp = 0.5;
+                else { double ch = std::cosh(p.stretch * s); xp = 0.5 * p.stretch / (ch * ch * std::tanh(p.stretch)); }
+                hxi[i] = 1.0 / (xp * I.ds);
+                hdx[i] = xp * I.ds;
+                xpmin = std::min(xpmin, xp);
+            }
+            I.dt = p.dt > 0 ? p.dt : p.cfl * xpmin * I.ds / xr.x[Q - 1];
+            double* hg = put(&I.gst, 21);
+            for (int r = 0; r < 3; ++r) stencil7(r, hg + 7 * r);
+        }
+        putw(&I.gL, L.K);
+        putw(&I.gR, L.K);
+        {
+            // sqrt(l) and 1/sqrt(l): recurrence of the orthonormal He_l/sqrt(l!)
+            double* hb = put(&I.fsq, QYMAX + 2);
+            double* hib = put(&I.fisq, QYMAX + 2);
+            for (int l = 0; l < QYMAX + 2; ++l) { hb[l] = std::sqrt((double)l); hib[l] = l ? 1.0 / std::sqrt((double)l) : 0.0; }
+        }
+        if (pos * 8 != L.tables) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: table layout mismatch"); }
+        regions.push_back({tab_off, L.tables});
+        {
+            size_t o = staging.size();
+            staging.resize(o + L.tables);
+            std::memcpy(staging.data() + o, img.data(), L.tables);
+        }
+        off += L.tables;
+        // state
+        for (int b = 0; b < 3; ++b) I.f[b] = take(L.fbuf);
+        I.node = reinterpret_cast<double*>(take(L.node));
+        I.tab = reinterpret_cast<double*>(take(L.tab));
+        I.misc = reinterpret_cast<double*>(take(L.misc));
+        I.status = c->d_status_all + ii;
+        I.steps = c->d_steps_all + ii;
+        c->inst.push_back(I);
+
+        int tiles = (N + TILE - 1) / TILE;
+        for (int t = 0; t < tiles; ++t) {
+            wm.push_back({ii, t * TILE, 0, L.K});
+            for (int k0 = 0; k0 < L.K; k0 += KC) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + KC)});
+        }
+        size_t sm = (size_t)L.ntab * TILE;
+        if (p.precision == FDLB_FP64) max_smem64 = std::max(max_smem64, sm * 8), c->any_fp64 = true;
+        else max_smem32 = std::max(max_smem32, sm * 4), c->any_fp32 = true;
+    }
+    if (off > need) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: workspace layout overflow"); }
+    c->smem_upd_f64 = max_smem64;
+    c->smem_upd_f32 = max_smem32;
+
+    // ---- upload
+    cudaStream_t s = c->stream;
+    int rc;
+    size_t so = 0;
+    for (auto& r : regions) {
+        rc = cuda_check(c, cudaMemcpyAsync(base + r.first, staging.data() + so, r.second, cudaMemcpyHostToDevice, s), "upload tables");
+        if (rc) { int e = rc; g_err = c->err; delete c; return e; }
+        so += r.second;
+    }
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s), "upload descriptors");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_mom, wm.data(), sizeof(Work) * n_mom, cudaMemcpyHostToDevice, s), "upload work");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_upd, wu.data(), sizeof(Work) * n_upd, cudaMemcpyHostToDevice, s), "upload work");
+    if (!rc) rc = cuda_check(c, launch_setup(c->d_inst, count, s), "setup kernel");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, n_mom, 0, c->any_fp64, c->any_fp32, s), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, count, 1, 0.0, c->d_resid_all, s), "residual kernel");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "fdlb_create synchronize");
+    if (rc) { int e = rc; g_err = c->err; delete c; return e; }
+    *out = c;
+    return FDLB_OK;
+}
+
+extern "C" void fdlb_destroy(fdlb_ctx* ctx) { delete ctx; }
+
+extern "C" int fdlb_info(const fdlb_ctx* ctx, int32_t inst, int32_t* nx, int32_t* nvel, double* dt) {
+    if (!ctx) return fail(nullptr, FDLB_EINVAL, "fdlb_info: null context");
+    if (inst < 0 || inst >= ctx->count) return fail(const_cast<fdlb_ctx*>(ctx), FDLB_EINVAL, "fdlb_info: instance out of range");
+    if (nx) *nx = ctx->inst[inst].N;
+    if (nvel) *nvel = ctx->inst[inst].K;
+    if (dt) *dt = ctx->inst[inst].dt;
+    return FDLB_OK;
+}
+
+extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_step: null context");
+    if (nsteps < 0 || !(freeze_tol >= 0)) return fail(c, FDLB_EINVAL, "fdlb_step: nsteps >= 0 and freeze_tol >= 0 required");
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = launch_step(c->d_inst, c->count, c->d_mom, c->n_mom, c->d_upd, c->n_upd, c->smem_upd_f64,
+                                    c->smem_upd_f32, c->any_fp64, c->any_fp32, freeze_tol, c->d_resid_all, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "fdlb_step launch");
+    }
+    return FDLB_OK;
+}
+
+extern "C" int fdlb_status(fdlb_ctx* c, double* residual, int32_t* status, int64_t* steps) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_status: null context");
+    int rc = FDLB_OK;
+    if (residual && !rc) rc = cuda_check(c, cudaMemcpyAsync(residual, c->d_resid_all, sizeof(double) * c->count, cudaMemcpyDeviceToHost, c->stream), "status copy");
+    if (status && !rc) rc = cuda_check(c, cudaMemcpyAsync(status, c->d_status_all, sizeof(int) * c->count, cudaMemcpyDeviceToHost, c->stream), "status copy");
+    std::vector<long long> st(c->count);
+    if (steps && !rc) rc = cuda_check(c, cudaMemcpyAsync(st.data(), c->d_steps_all, sizeof(long long) * c->count, cudaMemcpyDeviceToHost, c->stream), "status copy");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "status synchronize");
+    if (!rc && steps) for (int i = 0; i < c->count; ++i) steps[i] = st[i];
+    return rc;
+}
+
+extern "C" int fdlb_run(fdlb_ctx* c, double tol, int64_t max_steps, int64_t check_every, double timeout_s) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_run: null context");
+    if (!(tol > 0) || max_steps < 0 || check_every < 1 || !(timeout_s > 0)) return fail(c, FDLB_EINVAL, "fdlb_run: bad arguments");
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<int> st(c->count);
+    std::vector<long long> steps(c->count);
+    int64_t done = 0;
+    while (true) {
+        int rc = fdlb_status(c, nullptr, st.data(), nullptr);
+        if (rc) return rc;
+        bool active = false, nonfinite = false, unphys = false;
+        for (int s : st) {
+            active |= s == FDLB_ACTIVE;
+            nonfinite |= s == FDLB_FAILED_NONFINITE;
+            unphys |= s == FDLB_FAILED_UNPHYSICAL;
+        }
+        if (!active || done >= max_steps) {
+            if (nonfinite) return fail(c, FDLB_ENONFINITE, "an instance produced a non-finite moment");
+            if (unphys) return fail(c, FDLB_EUNPHYSICAL, "an instance produced n <= 0 or T <= 0");
+            return active ? 1 : FDLB_OK;
+        }
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(c, FDLB_ETIMEOUT, "fdlb_run: wall-clock limit reached");
+        int64_t chunk = std::min<int64_t>(check_every, max_steps - done);
+        rc = fdlb_step(c, chunk, tol);
+        if (rc) return rc;
+        done += chunk;
+    }
+}
+
+extern "C" int fdlb_moments(fdlb_ctx* c, int32_t inst, double* host_out) {
+    if (!c || !host_out) return fail(c, FDLB_EINVAL, "fdlb_moments: bad arguments");
+    if (inst < 0 || inst >= c->count) return fail(c, FDLB_EINVAL, "fdlb_moments: instance out of range");
+    const Inst& I = c->inst[inst];
+    int rc = cuda_check(c, cudaMemcpy2DAsync(host_out, sizeof(double) * I.N, I.node, sizeof(double) * I.ld,
+                                             sizeof(double) * I.N, 8, cudaMemcpyDeviceToHost, c->stream), "moments copy");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "moments synchronize");
+    return rc;
+}
+
+extern "C" int fdlb_set_profiles(fdlb_ctx* c, int32_t inst, const double* n, const double* uy, const double* T) {
+    if (!c || !n || !uy || !T) return fail(c, FDLB_EINVAL, "fdlb_set_profiles: bad arguments");
+    if (inst < 0 || inst >= c->count) return fail(c, FDLB_EINVAL, "fdlb_set_profiles: instance out of range");
+    const Inst& I = c->inst[inst];
+    std::vector<double> rows((size_t)4 * I.ld, 0.0);
+    for (int i = 0; i < I.N; ++i) {
+        if (!(n[i] > 0) || !(T[i] > 0) || !std::isfinite(uy[i])) return fail(c, FDLB_EINVAL, "fdlb_set_profiles: need n > 0, T > 0, finite u_y");
+        rows[0 * I.ld + i] = n[i];
+        rows[1 * I.ld + i] = 0.0;
+        rows[2 * I.ld + i] = uy[i];
+        rows[3 * I.ld + i] = T[i];
+    }
+    if (I.form == FORM_REDUCED1D) for (int i = 0; i < I.N; ++i) rows[2 * I.ld + i] = 0.0;
+    int rc = cuda_check(c, cudaMemcpyAsync(I.node, rows.data(), sizeof(double) * rows.size(), cudaMemcpyHostToDevice, c->stream), "profiles upload");
+    if (!rc) rc = cuda_check(c, launch_set_profiles(c->d_inst, inst, c->stream), "profiles kernel");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, c->count, inst, 0.0, c->d_resid_all, c->stream), "residual kernel");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "profiles synchronize");
+    return rc;
+}
+
+// ---- checkpoint: [magic u64][hash u64][steps i64][f bytes]
+static uint64_t param_hash(const fdlb_params& p) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&p);
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < sizeof(p); ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+extern "C" size_t fdlb_state_bytes(const fdlb_ctx* c, int32_t inst) {
+    if (!c || inst < 0 || inst >= c->count) return 0;
+    const Inst& I = c->inst[inst];
+    size_t es = I.precision == FDLB_FP64 ? 8 : 4;
+    return 24 + (size_t)I.K * I.ld * es;
+}
+
+extern "C" int fdlb_get_state(fdlb_ctx* c, int32_t inst, void* host, size_t bytes) {
+    if (!c || !host) return fail(c, FDLB_EINVAL, "fdlb_get_state: bad arguments");
+    size_t need = fdlb_state_bytes(c, inst);
+    if (need == 0 || bytes < need) return fail(c, FDLB_EINVAL, "fdlb_get_state: instance out of range or buffer too small");
+    const Inst& I = c->inst[inst];
+    uint64_t hdr[3] = {0x46444c42u, param_hash(c->prm[inst]), 0};
+    long long st = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&st, I.steps, sizeof(st), cudaMemcpyDeviceToHost, c->stream), "state copy");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(static_cast<char*>(host) + 24, I.f[0], need - 24, cudaMemcpyDeviceToHost, c->stream), "state copy");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "state synchronize");
+    if (rc) return rc;
+    hdr[2] = (uint64_t)st;
+    std::memcpy(host, hdr, 24);
+    return FDLB_OK;
+}
+
+extern "C" int fdlb_set_state(fdlb_ctx* c, int32_t inst, const void* host, size_t bytes) {
+    if (!c || !host) return fail(c, FDLB_EINVAL, "fdlb_set_state: bad arguments");
+    size_t need = fdlb_state_bytes(c, inst);
+    if (need == 0 || bytes != need) return fail(c, FDLB_ESTATE, "fdlb_set_state: size does not match this instance");
+    uint64_t hdr[3];
+    std::memcpy(hdr, host, 24);
+    if (hdr[0] != 0x46444c42u || hdr[1] != param_hash(c->prm[inst])) return fail(c, FDLB_ESTATE, "fdlb_set_state: state belongs to other parameters");
+    const Inst& I = c->inst[inst];
+    long long st = (long long)hdr[2];
+    int rc = cuda_check(c, cudaMemcpyAsync(I.f[0], static_cast<const char*>(host) + 24, need - 24, cudaMemcpyHostToDevice, c->stream), "state upload");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, c->count, inst, 0.0, c->d_resid_all, c->stream), "residual kernel");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.steps, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream), "state upload");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "state synchronize");
+    return rc;
+}

@@ -1,0 +1,88 @@
+// Internal layout shared by the host set-up (fdlb_host.cpp) and the kernels
+// (fdlb_kernels.cu).  Not part of the ABI.
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+
+namespace fdlb {
+
+constexpr int QMAX = 16;        // half-range order per side
+constexpr int QYMAX = 8;        // full-range order on y
+constexpr int QZMAX = 8;        // full-range order on z
+constexpr int TCMAX = QYMAX * QZMAX;
+constexpr int MX = 16;          // auxiliary half-range rule used for the x projections
+constexpr int MYMAX = 8;        // auxiliary full-range rule (exact: 2M > Q + 2)
+constexpr int NTERMS = 13;      // monomials of f^S + tau J1
+constexpr int TILE = 32;        // nodes per tile (one warp lane per node)
+
+enum Form : int { FORM_UNREDUCED = 0, FORM_REDUCED2D = 1, FORM_REDUCED1D = 2 };
+
+// Rows of the per-node primitive array (each row has ld doubles).
+enum NodeRow : int {
+    R_N = 0, R_UX, R_UY, R_T, R_QX, R_QY, R_PXX, R_PXY, R_SNEG, R_SPOS,
+    R_PREV_N, R_PREV_UX, R_PREV_UY, R_PREV_T,
+    NROWS
+};
+
+// Per-instance misc slots (doubles).
+enum Misc : int { M_NWL = 0, M_NWR, M_RESID, M_INL, M_INR, NMISC };
+
+// One channel problem as the kernels see it.  All pointers are device addresses
+// inside the caller's workspace.
+struct Inst {
+    int N, ld, Q, Qy, Qz, form, Tc, K;
+    int Mx, My, Mz;
+    int precision, j1_shear, pad0;
+    int ntab;                  // doubles per node in the projection table
+    int pad1;
+    double kn, eta0, chi0, mu0c, dt, ds, accel_y;
+    double T_L, T_R, U_L, U_R, T_init;
+    double x_h0;               // h_0 of the half-range orthonormal family
+    // tables
+    const double* px;          // [2Q]: +p_1..+p_Q, -p_1..-p_Q
+    const double* xq;          // [Mx] aux half-range nodes
+    const double* xw;          // [Mx] aux half-range weights
+    const double* xa;          // [Q]   recurrence alpha_l
+    const double* xb;          // [Q+1] recurrence b_l = sqrt(beta_l), b_0 = 0
+    const double* xib;         // [Q+1] 1/b_l (l >= 1)
+    const double* xH;          // [Q*Q] w_k h_l(p_k), index l*Q + k
+    const double* yn;          // [Qy] nodes
+    const double* yq;          // [My] aux full-range nodes
+    const double* yw;          // [My] aux full-range weights
+    const double* yH;          // [Qy*Qy] w_k h_l(p_k) with h_l = He_l/sqrt(l!)
+    const double* zn;          // [Qz]
+    const double* zq;          // [Mz]
+    const double* zw;          // [Mz]
+    const double* zH;          // [Qz*Qz]
+    const double* Ky;          // [Qy*Qy] d/dp_y kernel, row k, column k'
+    const double* tmt;         // [Tc] mass flag of transverse index t
+    const double* tpy;         // [Tc] p_y of t
+    const double* tet;         // [Tc] internal (z / theta) energy weight of t
+    const double* xpinv;       // [N] 1/(x'(s_i) ds)
+    const double* dxw;         // [N] x'(s_i) ds
+    const double* gst;         // [3*7] gradient weights (in s) for nodes 0,1,2 on nodes 0..6
+    const double* fsq;         // [QYMAX+2] sqrt(l)
+    const double* fisq;        // [QYMAX+2] 1/sqrt(l) (l >= 1)
+    double* gL;                // [K] unit-density wall Maxwellians
+    double* gR;                // [K]
+    void* f[3];                // RK buffers F, A, B; each K*ld elements of the storage type
+    double* node;              // [NROWS*ld]
+    double* tab;               // [ntab*ld] projection table (see below)
+    double* misc;              // [NMISC]
+    int* status;
+    long long* steps;
+};
+// Projection table layout per node i (column i of a row-major [ntab][ld] array):
+//   rows 0 .. 8Q-1          : Px[a][kx], a = 0..3, kx = 0..2Q-1   (row a*2Q + kx)
+//   rows 8Q .. 8Q+4Tc-1     : n * Y[a][t]                         (row 8Q + a*Tc + t)
+//   row  8Q+4Tc             : 1/tau
+// Target value at (kx, t) = sum_a Px[a][kx] * nY[a][t].
+
+// Work item for the tiled kernels.
+struct Work {
+    int inst;
+    int i0;      // first node of the tile
+    int k0, k1;  // velocity range [k0, k1)
+};
+
+}  // namespace fdlb

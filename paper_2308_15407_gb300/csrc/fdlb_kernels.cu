@@ -1,0 +1,697 @@
+// CUDA kernels of the FDLB solver for the simplified Enskog equation (sm_103a).
+//
+// One TVD-RK3 stage (Eq. rk3) is three kernels over a batch of independent channel
+// problems:
+//   k_moments  per node, reduce over all velocities: n, u, T, q, Pi (Eq. macro_LB)
+//              and the outgoing wall-flux partial sums;
+//   k_nodal    per node: chi (Eq. chi), Pr (Eq. prandtl), tau (Eqs. viscosity, tau),
+//              6th-order gradients (Sec. III B 3), the 13 monomial coefficients of
+//              f^S + tau J1 (Sec. II A, Eq. j1) and their projections onto the
+//              half-range (Sec. III A 2) and full-range (App. A) velocity sets;
+//              per instance: the wall densities n_w (Sec. III B);
+//   k_update   per (velocity, node): WENO-5 fluxes (Sec. III B 2) with the
+//              diffuse-reflection closure, the p_y-derivative force (App. A,
+//              Eq. kernel_H), relaxation to the projected target and the RK3
+//              combination.
+// After stage 3, k_moments of the new state and k_resid (per-step residual, status).
+//
+// Storage type S (double | float) holds f; compute type C of the per-velocity work
+// is double for FDLB_FP64 and float for FDLB_FP32_STORAGE.  Moments, gradients,
+// projections and the residual are always double.
+#include "fdlb_internal.h"
+#include "fdlb_launch.h"
+#include "../../include/fdlb.h"
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace fdlb {
+
+__constant__ int c_mono[NTERMS][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0},
+                                      {3, 0, 0}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 3, 0}, {0, 1, 2}};
+
+__device__ __forceinline__ double chi_cs(double eta) {
+    const double om = 1.0 - eta;
+    return (2.0 - eta) / (2.0 * om * om * om);
+}
+
+// ---------------------------------------------------------------------------
+// projections of (p - u)^a g(p; u, T), a = 0..3
+// ---------------------------------------------------------------------------
+
+// Half-range axis (Sec. III A 2): value at node +p_k (half = 0) of
+//   int_0^inf l_k(p) (p - u)^a g(p; u, T) dp,
+// or at node -p_k (half = 1), which is (-1)^a times the same with u -> -u.  Evaluated in
+// the orthonormal basis, value_k = w_k sum_l h_l(p_k) G_l, with
+//   G_l = int_0^inf h_l(p) (p - u)^a g dp = sum_m W_m exp(q_m v - v^2/2) h_l(sqrt(T) q_m) y_m^a,
+// p = sqrt(T) q, v = u/sqrt(T), y_m = sqrt(T) q_m - u, on the MX-point auxiliary rule.
+__device__ void proj_x(const Inst& I, double u, double T, int half, double* out, int stride) {
+    const int Q = I.Q;
+    double G[4][QMAX];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        for (int l = 0; l < QMAX; ++l) G[a][l] = 0.0;
+    const double uu = half ? -u : u;
+    const double sT = sqrt(T), v = uu / sT, ev = -0.5 * v * v;
+    for (int m = 0; m < MX; ++m) {
+        const double q = I.xq[m], x = sT * q;
+        const double E = I.xw[m] * exp(fma(q, v, ev));
+        const double y = x - uu;
+        const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+        double hm = 0.0, h = I.x_h0;
+        for (int l = 0; l < Q; ++l) {
+            G[0][l] = fma(E, h, G[0][l]);
+            G[1][l] = fma(e1, h, G[1][l]);
+            G[2][l] = fma(e2, h, G[2][l]);
+            G[3][l] = fma(e3, h, G[3][l]);
+            const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
+            hm = h;
+            h = hn;
+        }
+    }
+    for (int a = 0; a < 4; ++a) {
+        const double sgn = (half && (a & 1)) ? -1.0 : 1.0;
+        for (int k = 0; k < Q; ++k) {
+            double s = 0.0;
+            for (int l = 0; l < Q; ++l) s = fma(I.xH[l * Q + k], G[a][l], s);
+            out[(a * 2 * Q + half * Q + k) * stride] = sgn * s;
+        }
+    }
+}
+
+// Full-range axis (App. A): out[a*Qn + k] = int_R l_k(p) (p - u)^a g(p; u, T) dp, exact
+// with p = u + sqrt(T) y on the M-point Gauss-Hermite rule (2M - 1 >= Qn + 2).
+__device__ void proj_full(const Inst& I, const double* aq, const double* aw, const double* H, int Qn, int M, double u,
+                          double T, int amax, double* out) {
+    double G[4][QYMAX];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        for (int l = 0; l < QYMAX; ++l) G[a][l] = 0.0;
+    const double sT = sqrt(T);
+    for (int m = 0; m < M; ++m) {
+        const double y = sT * aq[m], x = u + y, E = aw[m];
+        const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+        double hm = 0.0, h = 1.0;
+        for (int l = 0; l < Qn; ++l) {
+            G[0][l] = fma(E, h, G[0][l]);
+            G[1][l] = fma(e1, h, G[1][l]);
+            G[2][l] = fma(e2, h, G[2][l]);
+            G[3][l] = fma(e3, h, G[3][l]);
+            const double hn = (x * h - I.fsq[l] * hm) * I.fisq[l + 1];
+            hm = h;
+            h = hn;
+        }
+    }
+    for (int a = 0; a <= amax; ++a)
+        for (int k = 0; k < Qn; ++k) {
+            double s = 0.0;
+            for (int l = 0; l < Qn; ++l) s = fma(H[l * Qn + k], G[a][l], s);
+            out[a * Qn + k] = s;
+        }
+}
+
+// E[xi^j] of a centred Gaussian of variance T.
+__device__ __forceinline__ double gmom(int j, double T) {
+    switch (j) {
+        case 0: return 1.0;
+        case 2: return T;
+        case 4: return 3.0 * T * T;
+        case 6: return 15.0 * T * T * T;
+        default: return 0.0;
+    }
+}
+
+// Transverse factors: out[(a*Tc + t)*stride] = nscale * sum_{terms with x-power a} c_term * Ytrans(t).
+__device__ void build_Y(const Inst& I, const double* c, double uy, double T, double nscale, double* out, int stride) {
+    const int Tc = I.Tc;
+    if (I.form == FORM_REDUCED1D) {
+        for (int a = 0; a < 4; ++a)
+            for (int slot = 0; slot < 2; ++slot) {
+                double s = 0.0;
+                for (int j = 0; j < NTERMS; ++j) {
+                    if (c_mono[j][0] != a) continue;
+                    const int b = c_mono[j][1], cc = c_mono[j][2];
+                    const double e = slot == 0 ? gmom(b, T) * gmom(cc, T)
+                                               : gmom(b + 2, T) * gmom(cc, T) + gmom(b, T) * gmom(cc + 2, T);
+                    s = fma(c[j], e, s);
+                }
+                out[(a * Tc + slot) * stride] = nscale * s;
+            }
+        return;
+    }
+    double Py[4 * QYMAX];
+    proj_full(I, I.yq, I.yw, I.yH, I.Qy, I.My, uy, T, 3, Py);
+    const int Qy = I.Qy;
+    if (I.form == FORM_UNREDUCED) {
+        double Pz[3 * QZMAX];
+        const int Qz = I.Qz;
+        proj_full(I, I.zq, I.zw, I.zH, Qz, I.Mz, 0.0, T, 2, Pz);
+        for (int a = 0; a < 4; ++a)
+            for (int t = 0; t < Tc; ++t) {
+                const int ky = t / Qz, kz = t - ky * Qz;
+                double s = 0.0;
+                for (int j = 0; j < NTERMS; ++j) {
+                    if (c_mono[j][0] != a) continue;
+                    s = fma(c[j], Py[c_mono[j][1] * Qy + ky] * Pz[c_mono[j][2] * Qz + kz], s);
+                }
+                out[(a * Tc + t) * stride] = nscale * s;
+            }
+    } else {
+        for (int a = 0; a < 4; ++a)
+            for (int t = 0; t < Tc; ++t) {
+                const int ky = t >> 1, slot = t & 1;
+                double s = 0.0;
+                for (int j = 0; j < NTERMS; ++j) {
+                    if (c_mono[j][0] != a) continue;
+                    const int cc = c_mono[j][2];
+                    const double zf = slot == 0 ? gmom(cc, T) : gmom(cc + 2, T);
+                    s = fma(c[j], Py[c_mono[j][1] * Qy + ky] * zf, s);
+                }
+                out[(a * Tc + t) * stride] = nscale * s;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// set-up: wall Maxwellians, initial state
+// ---------------------------------------------------------------------------
+__device__ void wall_maxwellian(const Inst& I, double U, double T, double* g) {
+    double Px[4 * 2 * QMAX];
+    proj_x(I, 0.0, T, 0, Px, 1);
+    proj_x(I, 0.0, T, 1, Px, 1);
+    double c[NTERMS];
+    for (int j = 0; j < NTERMS; ++j) c[j] = 0.0;
+    c[0] = 1.0;
+    double Y[4 * TCMAX];
+    build_Y(I, c, U, T, 1.0, Y, 1);
+    for (int k = 0; k < I.K; ++k) {
+        const int kx = k / I.Tc, t = k - kx * I.Tc;
+        g[k] = Px[kx] * Y[t];
+    }
+}
+
+__global__ void k_setup(Inst* insts) {
+    Inst& I = insts[blockIdx.x];
+    if (threadIdx.x == 0) wall_maxwellian(I, I.U_L, I.T_L, I.gL);
+    if (threadIdx.x == 32) wall_maxwellian(I, I.U_R, I.T_R, I.gR);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int Q = I.Q, Tc = I.Tc;
+        double inL = 0.0, inR = 0.0;
+        for (int k = 0; k < I.K; ++k) {
+            const int kx = k / Tc, t = k - kx * Tc;
+            const double mp = I.tmt[t] * I.px[kx];
+            if (kx < Q) inL = fma(mp, I.gL[k], inL);
+            else inR = fma(mp, I.gR[k], inR);
+        }
+        I.misc[M_INL] = inL;
+        I.misc[M_INR] = inR;
+        I.misc[M_NWL] = 1.0;
+        I.misc[M_NWR] = 1.0;
+        I.misc[M_RESID] = CUDART_INF;
+        *I.status = FDLB_ACTIVE;
+        *I.steps = 0;
+    }
+    const double T0 = I.T_init;
+    for (int i = threadIdx.x; i < I.ld; i += blockDim.x) {
+        I.node[R_N * I.ld + i] = 1.0;
+        I.node[R_UX * I.ld + i] = 0.0;
+        I.node[R_UY * I.ld + i] = 0.0;
+        I.node[R_T * I.ld + i] = T0;
+    }
+}
+
+// Projected local equilibrium from the profile rows into F (all instances when inst < 0).
+template <typename S>
+__global__ void k_profiles(Inst* insts, int inst) {
+    Inst& I = insts[inst < 0 ? blockIdx.x : inst];
+    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    const int ld = I.ld, Q = I.Q, Tc = I.Tc;
+    double c[NTERMS];
+    for (int j = 0; j < NTERMS; ++j) c[j] = 0.0;
+    c[0] = 1.0;
+    for (int i = threadIdx.x; i < I.N; i += blockDim.x) {
+        const double n = I.node[R_N * ld + i], uy = I.node[R_UY * ld + i], T = I.node[R_T * ld + i];
+        proj_x(I, 0.0, T, 0, I.tab + i, ld);
+        proj_x(I, 0.0, T, 1, I.tab + i, ld);
+        build_Y(I, c, uy, T, n, I.tab + 8 * Q * ld + i, ld);
+    }
+    __syncthreads();
+    S* F = static_cast<S*>(I.f[0]);
+    for (int k = 0; k < I.K; ++k) {
+        const int kx = k / Tc, t = k - kx * Tc;
+        for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+            double v = 0.0;
+            if (i < I.N)
+                for (int a = 0; a < 4; ++a) v = fma(I.tab[(a * 2 * Q + kx) * ld + i], I.tab[(8 * Q + a * Tc + t) * ld + i], v);
+            F[(size_t)k * ld + i] = (S)v;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *I.status = FDLB_ACTIVE;
+        *I.steps = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// moments
+// ---------------------------------------------------------------------------
+constexpr int MOM_WARPS = 8;
+constexpr int NSUM = 15;
+
+template <typename S>
+__global__ void __launch_bounds__(TILE * MOM_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
+    if (*I.status != FDLB_ACTIVE) return;
+    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    const int lane = threadIdx.x, g = threadIdx.y;
+    const int i = w.i0 + lane;
+    const int N = I.N, ld = I.ld, Tc = I.Tc, K = I.K, Q = I.Q;
+    const bool valid = i < N;
+    const S* f = static_cast<const S*>(I.f[buf]);
+    double acc[NSUM];
+#pragma unroll
+    for (int j = 0; j < NSUM; ++j) acc[j] = 0.0;
+    // s0 sneg spos sy sxx sxy syy se sxxx sxyy sxxy syyy sxe sye (14 used)
+    for (int k = g; k < K; k += MOM_WARPS) {
+        const int kx = k / Tc, t = k - kx * Tc;
+        const double fv = valid ? (double)f[(size_t)k * ld + i] : 0.0;
+        const double p = I.px[kx], py = I.tpy[t], mt = I.tmt[t], et = I.tet[t];
+        const double mf = mt * fv, ef = et * fv;
+        const double mfp = mf * p, mfy = mf * py;
+        acc[0] += mf;
+        if (kx >= Q) acc[1] += mfp; else acc[2] += mfp;
+        acc[3] += mfy;
+        acc[4] = fma(mfp, p, acc[4]);
+        acc[5] = fma(mfp, py, acc[5]);
+        acc[6] = fma(mfy, py, acc[6]);
+        acc[7] += ef;
+        acc[8] = fma(mfp * p, p, acc[8]);
+        acc[9] = fma(mfp * py, py, acc[9]);
+        acc[10] = fma(mfp * p, py, acc[10]);
+        acc[11] = fma(mfy * py, py, acc[11]);
+        acc[12] = fma(ef, p, acc[12]);
+        acc[13] = fma(ef, py, acc[13]);
+    }
+    __shared__ double red[NSUM][MOM_WARPS][TILE];
+#pragma unroll
+    for (int j = 0; j < NSUM; ++j) red[j][g][lane] = acc[j];
+    __syncthreads();
+    if (g != 0 || !valid) return;
+    double s[NSUM];
+#pragma unroll
+    for (int j = 0; j < NSUM; ++j) {
+        double v = 0.0;
+        for (int q = 0; q < MOM_WARPS; ++q) v += red[j][q][lane];
+        s[j] = v;
+    }
+    const double n = s[0], sx = s[1] + s[2];
+    const double ux = sx / n, uy = s[3] / n;
+    const double Pxx = s[4] - n * ux * ux, Pxy = s[5] - n * ux * uy, Pyy = s[6] - n * uy * uy;
+    const double E = 0.5 * (Pxx + Pyy) + s[7];
+    const double T = E / (1.5 * n);
+    const double cx3 = s[8] - 3.0 * ux * s[4] + 2.0 * n * ux * ux * ux;
+    const double cxyy = s[9] - 2.0 * uy * s[5] - ux * s[6] + 2.0 * n * ux * uy * uy;
+    const double cxxy = s[10] - 2.0 * ux * s[5] - uy * s[4] + 2.0 * n * ux * ux * uy;
+    const double cy3 = s[11] - 3.0 * uy * s[6] + 2.0 * n * uy * uy * uy;
+    const double qx = 0.5 * (cx3 + cxyy) + (s[12] - ux * s[7]);
+    const double qy = 0.5 * (cy3 + cxxy) + (s[13] - uy * s[7]);
+    double* nd = I.node;
+    nd[R_N * ld + i] = n;
+    nd[R_UX * ld + i] = ux;
+    nd[R_UY * ld + i] = uy;
+    nd[R_T * ld + i] = T;
+    nd[R_QX * ld + i] = qx;
+    nd[R_QY * ld + i] = qy;
+    nd[R_PXX * ld + i] = Pxx;
+    nd[R_PXY * ld + i] = Pxy;
+    nd[R_SNEG * ld + i] = s[1];
+    nd[R_SPOS * ld + i] = s[2];
+}
+
+// ---------------------------------------------------------------------------
+// per-node closure and projection tables
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_nodal(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.x];
+    if (*I.status != FDLB_ACTIVE) return;
+    const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc;
+    const double* nd = I.node;
+    if (threadIdx.x == 0) {
+        // zero net mass flux through each wall (Sec. III B): outgoing wall-face flux is the
+        // quadratic reconstruction (11 f_1 - 7 f_2 + 2 f_3)/6 of the outgoing populations.
+        const double oL = (11.0 * nd[R_SNEG * ld + 0] - 7.0 * nd[R_SNEG * ld + 1] + 2.0 * nd[R_SNEG * ld + 2]) / 6.0;
+        const double oR = (11.0 * nd[R_SPOS * ld + N - 1] - 7.0 * nd[R_SPOS * ld + N - 2] + 2.0 * nd[R_SPOS * ld + N - 3]) / 6.0;
+        I.misc[M_NWL] = -oL / I.misc[M_INL];
+        I.misc[M_NWR] = -oR / I.misc[M_INR];
+    }
+    const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
+    const double k_mu = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
+    const double k_pn = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
+    const double k_pd = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * CUDART_PI));
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double gn = 0.0, gc = 0.0, gT = 0.0, gux = 0.0, guy = 0.0;
+        for (int j = 0; j < 7; ++j) {
+            int idx;
+            double wj;
+            if (i < 3) { idx = j; wj = I.gst[i * 7 + j]; }
+            else if (i > N - 4) { const int m = N - 1 - i; idx = N - 1 - j; wj = -I.gst[m * 7 + j]; }
+            else { idx = i - 3 + j; wj = cen[j]; }
+            if (wj == 0.0) continue;
+            const double nj = nd[R_N * ld + idx], Tj = nd[R_T * ld + idx];
+            gn = fma(wj, log(nj), gn);
+            gc = fma(wj, log(chi_cs(I.eta0 * nj)), gc);
+            gT = fma(wj, log(Tj), gT);
+            gux = fma(wj, nd[R_UX * ld + idx], gux);
+            guy = fma(wj, nd[R_UY * ld + idx], guy);
+        }
+        const double xi = I.xpinv[i];
+        const double Gr = (2.0 * gn + gc + gT) * xi, Br = gT * xi, Ur = gux * xi, Vr = guy * xi;
+        const double n = nd[R_N * ld + i], ux = nd[R_UX * ld + i], uy = nd[R_UY * ld + i], T = nd[R_T * ld + i];
+        const double qx = nd[R_QX * ld + i], qy = nd[R_QY * ld + i];
+        const double eta = I.eta0 * n, chi = chi_cs(eta), br = 4.0 * eta, brc = br * chi;
+        const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_pn * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
+        const double mu = I.mu0c * sqrt(T) * (1.0 / chi + 0.8 * br + k_mu * br * br * chi);
+        const double tau = mu / (n * T);
+        // f^S + tau J1 = n g(xi) * sum_j c_j xi^(a_j, b_j, c_j)
+        const double A = (1.0 - Pr) / (5.0 * n * T * T), W = -tau * brc, iT = 1.0 / T;
+        double c[NTERMS];
+        c[0] = 1.0 - W * Ur;
+        c[1] = -5.0 * A * qx + W * (Gr - 1.5 * Br);
+        c[2] = -5.0 * A * qy;
+        c[3] = W * 0.6 * Ur * iT;
+        c[4] = W * 0.2 * Ur * iT;
+        c[5] = c[4];
+        c[6] = I.j1_shear ? W * 0.4 * Vr * iT : 0.0;
+        c[7] = A * qx * iT + W * 0.3 * Br * iT;
+        c[8] = c[7];
+        c[9] = c[7];
+        c[10] = A * qy * iT;
+        c[11] = c[10];
+        c[12] = c[10];
+        double* col = I.tab + i;
+        proj_x(I, ux, T, 0, col, ld);
+        proj_x(I, ux, T, 1, col, ld);
+        build_Y(I, c, uy, T, n, col + 8 * Q * ld, ld);
+        col[(8 * Q + 4 * Tc) * ld] = 1.0 / tau;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-step residual and status
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double tol, double* resid_all) {
+    Inst& I = insts[blockIdx.x];
+    const int ld = I.ld, N = I.N;
+    double* nd = I.node;
+    if (anchor >= -1) {
+        if (anchor >= 0 && anchor != (int)blockIdx.x) return;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            nd[R_PREV_N * ld + i] = nd[R_N * ld + i];
+            nd[R_PREV_UX * ld + i] = nd[R_UX * ld + i];
+            nd[R_PREV_UY * ld + i] = nd[R_UY * ld + i];
+            nd[R_PREV_T * ld + i] = nd[R_T * ld + i];
+        }
+        if (threadIdx.x == 0) {
+            I.misc[M_RESID] = CUDART_INF;
+            resid_all[blockIdx.x] = CUDART_INF;
+        }
+        return;
+    }
+    if (*I.status != FDLB_ACTIVE) return;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    int bad_nf = 0, bad_ph = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double n = nd[R_N * ld + i], ux = nd[R_UX * ld + i], uy = nd[R_UY * ld + i], T = nd[R_T * ld + i];
+        if (!isfinite(n) || !isfinite(ux) || !isfinite(uy) || !isfinite(T)) bad_nf = 1;
+        else if (!(n > 0.0) || !(T > 0.0)) bad_ph = 1;
+        const double w = I.dxw[i];
+        const double dn = n - nd[R_PREV_N * ld + i], dT = T - nd[R_PREV_T * ld + i];
+        const double dux = ux - nd[R_PREV_UX * ld + i], duy = uy - nd[R_PREV_UY * ld + i];
+        s[0] += w * dn * dn;
+        s[1] += w * n * n;
+        s[2] += w * dT * dT;
+        s[3] += w * T * T;
+        s[4] += w * dux * dux;
+        s[5] += w * duy * duy;
+        nd[R_PREV_N * ld + i] = n;
+        nd[R_PREV_UX * ld + i] = ux;
+        nd[R_PREV_UY * ld + i] = uy;
+        nd[R_PREV_T * ld + i] = T;
+    }
+    __shared__ double red[6][8];
+    __shared__ int flags[2];
+    if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; }
+    __syncthreads();
+    if (bad_nf) atomicOr(&flags[0], 1);
+    if (bad_ph) atomicOr(&flags[1], 1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double v = s[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[j][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[6];
+        for (int j = 0; j < 6; ++j) {
+            t[j] = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t[j] += red[j][q];
+        }
+        double r = fmax(fmax(sqrt(t[0] / t[1]), sqrt(t[2] / t[3])), fmax(sqrt(t[4]), sqrt(t[5])));
+        *I.steps += 1;
+        I.misc[M_RESID] = r;
+        resid_all[blockIdx.x] = r;
+        if (flags[0]) *I.status = FDLB_FAILED_NONFINITE;
+        else if (flags[1]) *I.status = FDLB_FAILED_UNPHYSICAL;
+        else if (tol > 0.0 && r < tol) *I.status = FDLB_CONVERGED;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// update: WENO-5 advection + walls + force + relaxation + RK3 combination
+// ---------------------------------------------------------------------------
+
+// Upwind-biased WENO-5 face value from (f_{i-2}, f_{i-1}, f_i, f_{i+1}, f_{i+2}) taken in the
+// upwind direction (Sec. III B 2).  Weights delta_q/phi_q^2 without epsilon; a vanishing
+// indicator takes the weight in the limit (the normalised weights are continuous there).
+__device__ __forceinline__ double weno_face(double a, double b, double c, double d, double e) {
+    const double F1 = fma(1.0 / 3.0, a, fma(-7.0 / 6.0, b, 11.0 / 6.0 * c));
+    const double F2 = fma(-1.0 / 6.0, b, fma(5.0 / 6.0, c, 1.0 / 3.0 * d));
+    const double F3 = fma(1.0 / 3.0, c, fma(5.0 / 6.0, d, -1.0 / 6.0 * e));
+    const double t1 = a - 2.0 * b + c, t2 = a - 4.0 * b + 3.0 * c;
+    const double u1 = b - 2.0 * c + d, u2 = b - d;
+    const double v1 = c - 2.0 * d + e, v2 = 3.0 * c - 4.0 * d + e;
+    const double s1 = fma(13.0 / 12.0, t1 * t1, 0.25 * t2 * t2);
+    const double s2 = fma(13.0 / 12.0, u1 * u1, 0.25 * u2 * u2);
+    const double s3 = fma(13.0 / 12.0, v1 * v1, 0.25 * v2 * v2);
+    const double smax = fmax(s1, fmax(s2, s3));
+    double w1, w2, w3;
+    if (smax == 0.0) {
+        w1 = 0.1; w2 = 0.6; w3 = 0.3;
+    } else {
+        // omega_q ~ delta_q / phi_q^2 ~ delta_q prod_{r != q} phi_r^2 (phi scaled by the max)
+        const double r = 1.0 / smax;
+        const double a1 = s1 * r, a2 = s2 * r, a3 = s3 * r;
+        const double p1 = a1 * a1, p2 = a2 * a2, p3 = a3 * a3;
+        w1 = 0.1 * p2 * p3;
+        w2 = 0.6 * p1 * p3;
+        w3 = 0.3 * p1 * p2;
+        double sum = w1 + w2 + w3;
+        if (sum == 0.0) {
+            // two indicators vanish (or underflow): weight on the smallest ones
+            const double smin = fmin(s1, fmin(s2, s3));
+            w1 = s1 == smin ? 0.1 : 0.0;
+            w2 = s2 == smin ? 0.6 : 0.0;
+            w3 = s3 == smin ? 0.3 : 0.0;
+            sum = w1 + w2 + w3;
+        }
+        const double is = 1.0 / sum;
+        w1 *= is; w2 *= is; w3 *= is;
+    }
+    return fma(w1, F1, fma(w2, F2, w3 * F3));
+}
+
+__device__ __forceinline__ float weno_face(float a, float b, float c, float d, float e) {
+    const float F1 = fmaf(1.0f / 3.0f, a, fmaf(-7.0f / 6.0f, b, 11.0f / 6.0f * c));
+    const float F2 = fmaf(-1.0f / 6.0f, b, fmaf(5.0f / 6.0f, c, 1.0f / 3.0f * d));
+    const float F3 = fmaf(1.0f / 3.0f, c, fmaf(5.0f / 6.0f, d, -1.0f / 6.0f * e));
+    const float t1 = a - 2.0f * b + c, t2 = a - 4.0f * b + 3.0f * c;
+    const float u1 = b - 2.0f * c + d, u2 = b - d;
+    const float v1 = c - 2.0f * d + e, v2 = 3.0f * c - 4.0f * d + e;
+    const float s1 = fmaf(13.0f / 12.0f, t1 * t1, 0.25f * t2 * t2);
+    const float s2 = fmaf(13.0f / 12.0f, u1 * u1, 0.25f * u2 * u2);
+    const float s3 = fmaf(13.0f / 12.0f, v1 * v1, 0.25f * v2 * v2);
+    const float smin = fminf(s1, fminf(s2, s3));
+    float w1, w2, w3;
+    if (smin == 0.0f) {
+        w1 = s1 == 0.0f ? 0.1f : 0.0f;
+        w2 = s2 == 0.0f ? 0.6f : 0.0f;
+        w3 = s3 == 0.0f ? 0.3f : 0.0f;
+    } else {
+        // delta_q (phi_min/phi_q)^2: no overflow or underflow of the sum
+        const float r1 = smin / s1, r2 = smin / s2, r3 = smin / s3;
+        w1 = 0.1f * r1 * r1;
+        w2 = 0.6f * r2 * r2;
+        w3 = 0.3f * r3 * r3;
+    }
+    const float is = 1.0f / (w1 + w2 + w3);
+    return fmaf(w1 * is, F1, fmaf(w2 * is, F2, w3 * is * F3));
+}
+
+constexpr int UPD_WARPS = 8;
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restrict__ insts, const Work* __restrict__ work, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* stab = reinterpret_cast<C*>(smem_raw);
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
+    if (*I.status != FDLB_ACTIVE) return;
+    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const int i = w.i0 + lane;
+    const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, ntab = I.ntab;
+    const bool valid = i < N;
+    for (int r = wy; r < ntab; r += UPD_WARPS) stab[r * TILE + lane] = valid ? (C)I.tab[(size_t)r * ld + i] : (C)0;
+    __syncthreads();
+    const S* src = static_cast<const S*>(I.f[stage - 1]);
+    S* dst = static_cast<S*>(I.f[stage % 3]);
+    const S* F = static_cast<const S*>(I.f[0]);
+    const C ca = stage == 1 ? (C)0 : (stage == 2 ? (C)0.75 : (C)(1.0 / 3.0));
+    const C cb = stage == 1 ? (C)1 : (stage == 2 ? (C)0.25 : (C)(2.0 / 3.0));
+    const C dt = (C)I.dt;
+    const C nwL = (C)I.misc[M_NWL], nwR = (C)I.misc[M_NWR];
+    const C xpi = valid ? (C)I.xpinv[i] : (C)0;
+    const C invtau = stab[(8 * Q + 4 * Tc) * TILE + lane];
+    const bool force = I.accel_y != 0.0 && I.form != FORM_REDUCED1D;
+    const int Tz = I.form == FORM_UNREDUCED ? I.Qz : 2;
+    const C ay = (C)I.accel_y;
+    const C sixth = (C)(1.0 / 6.0);
+    for (int k = w.k0 + wy; k < w.k1; k += UPD_WARPS) {
+        const int kx = k / Tc, t = k - kx * Tc;
+        const bool pos = kx < Q;
+        const C p = (C)I.px[kx];
+        const S* row = src + (size_t)k * ld;
+        // node values i-3 .. i+3 with ghost cells (Sec. III B): incoming populations take the
+        // wall Maxwellian n_w g; outgoing ones the quadratic extrapolation of nodes 0..2.
+        C v[7];
+#pragma unroll
+        for (int jj = 0; jj < 7; ++jj) {
+            const int j = i - 3 + jj;
+            C val;
+            if (j >= 0 && j < N) {
+                val = (C)row[j];
+            } else if (j < 0) {
+                if (pos) {
+                    val = nwL * (C)I.gL[k];
+                } else {
+                    const C f0 = (C)row[0], f1 = (C)row[1], f2 = (C)row[2];
+                    val = j == -1 ? 3 * f0 - 3 * f1 + f2 : (j == -2 ? 6 * f0 - 8 * f1 + 3 * f2 : 10 * f0 - 15 * f1 + 6 * f2);
+                }
+            } else {
+                if (!pos) {
+                    val = nwR * (C)I.gR[k];
+                } else {
+                    const C f0 = (C)row[N - 1], f1 = (C)row[N - 2], f2 = (C)row[N - 3];
+                    val = j == N ? 3 * f0 - 3 * f1 + f2 : (j == N + 1 ? 6 * f0 - 8 * f1 + 3 * f2 : 10 * f0 - 15 * f1 + 6 * f2);
+                }
+            }
+            v[jj] = val;
+        }
+        // right face (i + 1/2)
+        C fr;
+        if (i + 1 == N) fr = pos ? (11 * v[3] - 7 * v[2] + 2 * v[1]) * sixth : nwR * (C)I.gR[k];
+        else fr = pos ? weno_face(v[1], v[2], v[3], v[4], v[5]) : weno_face(v[6], v[5], v[4], v[3], v[2]);
+        C fl = __shfl_up_sync(0xffffffffu, fr, 1);
+        if (lane == 0) {
+            if (i == 0) fl = pos ? nwL * (C)I.gL[k] : (11 * v[3] - 7 * v[4] + 2 * v[5]) * sixth;
+            else fl = pos ? weno_face(v[0], v[1], v[2], v[3], v[4]) : weno_face(v[5], v[4], v[3], v[2], v[1]);
+        }
+        if (!valid) continue;
+        C L = -xpi * p * (fr - fl);
+        if (force) {
+            const int ky = t / Tz, kz = t - ky * Tz;
+            const double* Kr = I.Ky + ky * I.Qy;
+            C d = 0;
+            for (int kp = 0; kp < I.Qy; ++kp) d += (C)Kr[kp] * (C)src[(size_t)(kx * Tc + kp * Tz + kz) * ld + i];
+            L -= ay * d;
+        }
+        C tgt = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tgt += stab[(a * 2 * Q + kx) * TILE + lane] * stab[(8 * Q + a * Tc + t) * TILE + lane];
+        const C fi = v[3];
+        L += (tgt - fi) * invtau;
+        C out = cb * (fi + dt * L);
+        if (stage != 1) out += ca * (C)F[(size_t)k * ld + i];
+        dst[(size_t)k * ld + i] = (S)out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+cudaError_t launch_setup(const Inst* d_inst, int count, cudaStream_t s) {
+    k_setup<<<count, 128, 0, s>>>(const_cast<Inst*>(d_inst));
+    k_profiles<double><<<count, 128, 0, s>>>(const_cast<Inst*>(d_inst), -1);
+    k_profiles<float><<<count, 128, 0, s>>>(const_cast<Inst*>(d_inst), -1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_profiles(const Inst* d_inst, int inst, cudaStream_t s) {
+    k_profiles<double><<<1, 128, 0, s>>>(const_cast<Inst*>(d_inst), inst);
+    k_profiles<float><<<1, 128, 0, s>>>(const_cast<Inst*>(d_inst), inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const Inst* d_inst, const Work* d_mom, int n_mom, int buf, bool f64, bool f32, cudaStream_t s) {
+    dim3 blk(TILE, MOM_WARPS);
+    if (f64) k_moments<double><<<n_mom, blk, 0, s>>>(d_inst, d_mom, buf);
+    if (f32) k_moments<float><<<n_mom, blk, 0, s>>>(d_inst, d_mom, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid(const Inst* d_inst, int count, int anchor_inst, double freeze_tol, double* d_resid_all, cudaStream_t s) {
+    k_resid<<<count, 256, 0, s>>>(const_cast<Inst*>(d_inst), anchor_inst, freeze_tol, d_resid_all);
+    return cudaGetLastError();
+}
+
+static cudaError_t set_smem(size_t smem64, size_t smem32) {
+    static size_t done64 = 0, done32 = 0;
+    cudaError_t e = cudaSuccess;
+    if (smem64 > 48 * 1024 && smem64 > done64) {
+        e = cudaFuncSetAttribute(k_update<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+        if (e == cudaSuccess) done64 = smem64;
+    }
+    if (e == cudaSuccess && smem32 > 48 * 1024 && smem32 > done32) {
+        e = cudaFuncSetAttribute(k_update<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        if (e == cudaSuccess) done32 = smem32;
+    }
+    return e;
+}
+
+cudaError_t launch_step(const Inst* d_inst, int count, const Work* d_mom, int n_mom, const Work* d_upd, int n_upd,
+                        size_t smem64, size_t smem32, bool f64, bool f32, double freeze_tol, double* d_resid_all,
+                        cudaStream_t s) {
+    cudaError_t e = set_smem(smem64, smem32);
+    if (e != cudaSuccess) return e;
+    dim3 blk(TILE, UPD_WARPS);
+    for (int stage = 1; stage <= 3; ++stage) {
+        if (stage > 1) {
+            e = launch_moments(d_inst, d_mom, n_mom, stage - 1, f64, f32, s);
+            if (e != cudaSuccess) return e;
+        }
+        k_nodal<<<count, 128, 0, s>>>(d_inst);
+        if (f64) k_update<double, double><<<n_upd, blk, smem64, s>>>(d_inst, d_upd, stage);
+        if (f32) k_update<float, float><<<n_upd, blk, smem32, s>>>(d_inst, d_upd, stage);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_moments(d_inst, d_mom, n_mom, 0, f64, f32, s);
+    if (e != cudaSuccess) return e;
+    return launch_resid(d_inst, count, -2, freeze_tol, d_resid_all, s);
+}
+
+}  // namespace fdlb

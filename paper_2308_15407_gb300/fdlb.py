@@ -1,0 +1,221 @@
+"""ctypes binding of the C ABI in include/fdlb.h (argument marshalling only).
+
+Every step of the solver runs in the CUDA kernels of libfdlb.so.  PyTorch is used
+only to allocate the device workspace and to name the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field, fields
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdlb.so")
+
+FDLB_OK, FDLB_EINVAL, FDLB_ENOMEM, FDLB_ECUDA, FDLB_ENONFINITE, FDLB_EUNPHYSICAL, FDLB_ETIMEOUT, FDLB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+FOURIER, COUETTE, POISEUILLE = 0, 1, 2
+GRID_UNIFORM, GRID_TANH = 0, 1
+FP64, FP32_STORAGE = 0, 1
+ACTIVE, CONVERGED, FAILED_NONFINITE, FAILED_UNPHYSICAL = 0, 1, 2, 3
+MOMENT_ROWS = ("n", "ux", "uy", "T", "qx", "qy", "Pxx", "Pxy")
+
+
+class CParams(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("flow", C.c_int32), ("nx", C.c_int32), ("grid", C.c_int32),
+                ("qx_half", C.c_int32), ("qy", C.c_int32), ("qz", C.c_int32), ("precision", C.c_int32),
+                ("j1_shear", C.c_int32), ("reserved", C.c_int32), ("stretch", C.c_double), ("kn", C.c_double),
+                ("eta0", C.c_double), ("T_left", C.c_double), ("T_right", C.c_double), ("U_left", C.c_double),
+                ("U_right", C.c_double), ("accel_y", C.c_double), ("cfl", C.c_double), ("dt", C.c_double),
+                ("T_init", C.c_double)]
+
+
+@dataclass
+class Params:
+    """One channel problem (field meanings as in ``fdlb_params``)."""
+    nx: int
+    qx_half: int
+    qy: int
+    qz: int
+    kn: float
+    eta0: float
+    T_left: float = 1.0
+    T_right: float = 1.0
+    U_left: float = 0.0
+    U_right: float = 0.0
+    accel_y: float = 0.0
+    grid: str = "uniform"
+    stretch: float = 1.5
+    cfl: float = 0.5
+    dt: float = 0.0
+    j1_shear: bool = False
+    flow: int = FOURIER
+    T_init: float = 0.0
+    precision: str = "fp64"
+
+    def to_c(self) -> CParams:
+        p = CParams()
+        p.struct_size = C.sizeof(CParams)
+        p.flow = int(self.flow)
+        p.nx = int(self.nx)
+        p.grid = {"uniform": GRID_UNIFORM, "tanh": GRID_TANH}[self.grid]
+        p.qx_half, p.qy, p.qz = int(self.qx_half), int(self.qy), int(self.qz)
+        p.precision = {"fp64": FP64, "fp32": FP32_STORAGE}[self.precision]
+        p.j1_shear = int(bool(self.j1_shear))
+        p.reserved = 0
+        p.stretch, p.kn, p.eta0 = float(self.stretch), float(self.kn), float(self.eta0)
+        p.T_left, p.T_right, p.U_left, p.U_right = float(self.T_left), float(self.T_right), float(self.U_left), float(self.U_right)
+        p.accel_y, p.cfl, p.dt, p.T_init = float(self.accel_y), float(self.cfl), float(self.dt), float(self.T_init)
+        return p
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libfdlb.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2308_15407_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER(CParams)
+    vp, dp, ip, lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    sig = {
+        "fdlb_abi_version": (C.c_int32, []),
+        "fdlb_last_error": (C.c_char_p, [vp]),
+        "fdlb_workspace_bytes": (C.c_size_t, [P, C.c_int32]),
+        "fdlb_create": (C.c_int, [C.POINTER(vp), P, C.c_int32, vp, C.c_size_t, vp]),
+        "fdlb_destroy": (None, [vp]),
+        "fdlb_info": (C.c_int, [vp, C.c_int32, ip, ip, dp]),
+        "fdlb_step": (C.c_int, [vp, C.c_int64, C.c_double]),
+        "fdlb_run": (C.c_int, [vp, C.c_double, C.c_int64, C.c_int64, C.c_double]),
+        "fdlb_moments": (C.c_int, [vp, C.c_int32, dp]),
+        "fdlb_status": (C.c_int, [vp, dp, ip, lp]),
+        "fdlb_set_profiles": (C.c_int, [vp, C.c_int32, dp, dp, dp]),
+        "fdlb_state_bytes": (C.c_size_t, [vp, C.c_int32]),
+        "fdlb_get_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
+        "fdlb_set_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
+        "fdlb_quadrature": (C.c_int, [C.c_int32, C.c_int32, dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FdlbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fdlb error {code}: {msg}")
+        self.code = code
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def quadrature(kind: str, q: int):
+    """The library's own Gauss rule: kind 'half' (Sec. III A 2) or 'full' (App. A)."""
+    lib = load()
+    x = np.zeros(q)
+    w = np.zeros(q)
+    rc = lib.fdlb_quadrature({"half": 0, "full": 1}[kind], q, _dptr(x), _dptr(w))
+    if rc != FDLB_OK:
+        raise FdlbError(rc, lib.fdlb_last_error(None).decode())
+    return x, w
+
+
+def workspace_bytes(params) -> int:
+    lib = load()
+    arr = (CParams * len(params))(*[p.to_c() for p in params])
+    n = lib.fdlb_workspace_bytes(arr, len(params))
+    if n == 0:
+        raise FdlbError(FDLB_EINVAL, lib.fdlb_last_error(None).decode())
+    return n
+
+
+class Solver:
+    """A batch of channel problems living in one device workspace."""
+
+    def __init__(self, params, device="cuda", stream=None):
+        import torch
+        self.lib = load()
+        if isinstance(params, Params):
+            params = [params]
+        self.params = list(params)
+        self.count = len(self.params)
+        arr = (CParams * self.count)(*[p.to_c() for p in self.params])
+        nbytes = self.lib.fdlb_workspace_bytes(arr, self.count)
+        if nbytes == 0:
+            raise FdlbError(FDLB_EINVAL, self.lib.fdlb_last_error(None).decode())
+        self.device = torch.device(device)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = C.c_void_p()
+        rc = self.lib.fdlb_create(C.byref(self.ctx), arr, self.count, C.c_void_p(ptr), nbytes,
+                                  C.c_void_p(self.stream.cuda_stream))
+        if rc != FDLB_OK:
+            raise FdlbError(rc, self.lib.fdlb_last_error(None).decode())
+        self.nx, self.nvel, self.dt = [], [], []
+        for i in range(self.count):
+            nx, nv, dt = C.c_int32(), C.c_int32(), C.c_double()
+            self._check(self.lib.fdlb_info(self.ctx, i, C.byref(nx), C.byref(nv), C.byref(dt)))
+            self.nx.append(nx.value)
+            self.nvel.append(nv.value)
+            self.dt.append(dt.value)
+
+    def _check(self, rc):
+        if rc < 0:
+            raise FdlbError(rc, self.lib.fdlb_last_error(self.ctx).decode())
+        return rc
+
+    def close(self):
+        if self.ctx:
+            self.lib.fdlb_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps: int = 1, freeze_tol: float = 0.0):
+        self._check(self.lib.fdlb_step(self.ctx, int(nsteps), float(freeze_tol)))
+        return self
+
+    def run(self, tol: float, max_steps: int, check_every: int = 100, timeout_s: float = 3600.0) -> int:
+        return self._check(self.lib.fdlb_run(self.ctx, float(tol), int(max_steps), int(check_every), float(timeout_s)))
+
+    def moments(self, inst: int = 0) -> dict:
+        out = np.zeros((8, self.nx[inst]))
+        self._check(self.lib.fdlb_moments(self.ctx, inst, _dptr(out)))
+        return {k: out[j].copy() for j, k in enumerate(MOMENT_ROWS)}
+
+    def status(self):
+        r = np.zeros(self.count)
+        s = np.zeros(self.count, dtype=np.int32)
+        st = np.zeros(self.count, dtype=np.int64)
+        self._check(self.lib.fdlb_status(self.ctx, _dptr(r), s.ctypes.data_as(C.POINTER(C.c_int32)),
+                                         st.ctypes.data_as(C.POINTER(C.c_int64))))
+        return r, s, st
+
+    def set_profiles(self, inst: int, n, uy, T):
+        n, uy, T = (np.ascontiguousarray(x, dtype=np.float64) for x in (n, uy, T))
+        self._check(self.lib.fdlb_set_profiles(self.ctx, inst, _dptr(n), _dptr(uy), _dptr(T)))
+
+    def get_state(self, inst: int = 0) -> bytes:
+        nb = self.lib.fdlb_state_bytes(self.ctx, inst)
+        buf = C.create_string_buffer(nb)
+        self._check(self.lib.fdlb_get_state(self.ctx, inst, buf, nb))
+        return buf.raw
+
+    def set_state(self, inst: int, state: bytes):
+        buf = C.create_string_buffer(state, len(state))
+        self._check(self.lib.fdlb_set_state(self.ctx, inst, buf, len(state)))

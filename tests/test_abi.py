@@ -1,0 +1,74 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol include/fdlb.h
+declares, validates parameters, and its host-side Gauss rules match the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import quadrature as qd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fdlb.h")
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2308_15407_gb300 import fdlb
+    if not os.path.exists(fdlb.LIB_PATH):
+        from paper_2308_15407_gb300 import build
+        build.build()
+    return fdlb
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdlb_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(F):
+    lib = ctypes.CDLL(F.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_abi_version_and_struct(F):
+    lib = F.load()
+    assert lib.fdlb_abi_version() == 1
+    assert ctypes.sizeof(F.CParams) == 4 * 10 + 8 * 11
+
+
+def test_parameter_validation(F):
+    ok = F.Params(nx=50, qx_half=4, qy=4, qz=4, kn=0.1, eta0=0.1)
+    assert F.workspace_bytes([ok]) > 0
+    bad = [dict(nx=4), dict(qx_half=0), dict(qx_half=17), dict(qy=1), dict(qz=2), dict(qy=0, qz=4),
+           dict(eta0=0.5), dict(kn=0.0), dict(T_left=0.0), dict(qy=0, qz=0, U_left=0.1)]
+    for kw in bad:
+        p = F.Params(**{**ok.__dict__, **kw})
+        with pytest.raises(F.FdlbError):
+            F.workspace_bytes([p])
+    c = ok.to_c()
+    c.struct_size = 8
+    lib = F.load()
+    assert lib.fdlb_workspace_bytes((F.CParams * 1)(c), 1) == 0
+    assert b"struct_size" in lib.fdlb_last_error(None)
+
+
+@pytest.mark.parametrize("Q", [1, 2, 4, 6, 8, 12, 16])
+def test_library_half_range_rule_matches_oracle(F, Q):
+    x, w = F.quadrature("half", Q)
+    r = qd.half_range_rule(Q)
+    np.testing.assert_allclose(x, r.nodes, rtol=2e-15, atol=1e-14)
+    np.testing.assert_allclose(w, r.weights, rtol=5e-14, atol=1e-17)
+
+
+@pytest.mark.parametrize("Q", [2, 3, 4, 6, 8])
+def test_library_full_range_rule_matches_oracle(F, Q):
+    x, w = F.quadrature("full", Q)
+    r = qd.full_range_rule(Q)
+    np.testing.assert_allclose(x, r.nodes, atol=1e-14)
+    np.testing.assert_allclose(w, r.weights, rtol=1e-14)
