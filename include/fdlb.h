@@ -154,6 +154,15 @@ size_t fdlb_state_bytes(const fdlb_ctx* ctx, int32_t inst);
 int fdlb_get_state(fdlb_ctx* ctx, int32_t inst, void* host, size_t bytes);
 int fdlb_set_state(fdlb_ctx* ctx, int32_t inst, const void* host, size_t bytes);
 
+/* Optional per-kernel timing with CUDA events recorded on the context's stream around every
+ * launch (off by default).  fdlb_profile(ctx, 1) clears the records and starts recording,
+ * fdlb_profile(ctx, 0) stops.  fdlb_profile_read synchronises and returns, for kernel class
+ * kind (0 moments, 1 per-node closure, 2 update, 3 residual), the summed duration in ms and
+ * the number of launches recorded.  A launch of a class may run one kernel per storage
+ * precision present in the batch. */
+int fdlb_profile(fdlb_ctx* ctx, int32_t on);
+int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
+
 /* Host-only: the library's own Gauss rules (for checking the tables; no GPU needed).
  * kind 0 = half-range Gauss-Hermite on [0, inf) (Sec. III A 2), kind 1 = full-range (App. A);
  * weights are normalised to the weight omega(p) = exp(-p^2/2)/sqrt(2 pi).  nodes/weights

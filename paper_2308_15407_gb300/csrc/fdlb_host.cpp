@@ -45,7 +45,51 @@ struct fdlb_ctx {
     size_t smem_upd_f64 = 0, smem_upd_f32 = 0;
     bool any_fp32 = false, any_fp64 = false;
     std::string err;
+    // optional per-kernel-class event timing (fdlb_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev[KK_COUNT];
+    size_t nev[KK_COUNT] = {0, 0, 0, 0};
+    ~fdlb_ctx() {
+        for (auto& v : ev)
+            for (auto e : v) cudaEventDestroy(e);
+    }
 };
+
+// Record a start/stop event pair around one launch of class `kind` when profiling is on.
+static cudaError_t prof_mark(fdlb_ctx* c, int kind) {
+    if (!c->prof) return cudaSuccess;
+    auto& v = c->ev[kind];
+    if (c->nev[kind] >= v.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        v.push_back(e);
+    }
+    return cudaEventRecord(v[c->nev[kind]++], c->stream);
+}
+
+// One TVD-RK3 step (Eq. rk3): three stages of moments -> closure -> update, then the
+// moments of the new state and the residual/status pass.  The stage-1 moments are the
+// end-of-step moments of the previous step.
+static cudaError_t step_once(fdlb_ctx* c, double freeze_tol) {
+    cudaError_t e = cudaSuccess;
+    auto guard = [&](int kind, auto&& fn) {
+        if (e != cudaSuccess) return;
+        e = prof_mark(c, kind);
+        if (e == cudaSuccess) e = fn();
+        if (e == cudaSuccess) e = prof_mark(c, kind);
+    };
+    for (int stage = 1; stage <= 3; ++stage) {
+        if (stage > 1)
+            guard(KK_MOMENTS, [&] { return launch_moments(c->d_inst, c->d_mom, c->n_mom, stage - 1, c->any_fp64, c->any_fp32, c->stream); });
+        guard(KK_NODAL, [&] { return launch_nodal(c->d_inst, c->count, c->stream); });
+        guard(KK_UPDATE, [&] { return launch_update(c->d_inst, c->d_upd, c->n_upd, stage, c->smem_upd_f64, c->smem_upd_f32,
+                                                    c->any_fp64, c->any_fp32, c->stream); });
+    }
+    guard(KK_MOMENTS, [&] { return launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream); });
+    guard(KK_RESID, [&] { return launch_resid(c->d_inst, c->count, -2, freeze_tol, c->d_resid_all, c->stream); });
+    return e;
+}
 
 static int fail(fdlb_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
@@ -580,8 +624,7 @@ extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
     if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_step: null context");
     if (nsteps < 0 || !(freeze_tol >= 0)) return fail(c, FDLB_EINVAL, "fdlb_step: nsteps >= 0 and freeze_tol >= 0 required");
     for (int64_t s = 0; s < nsteps; ++s) {
-        cudaError_t e = launch_step(c->d_inst, c->count, c->d_mom, c->n_mom, c->d_upd, c->n_upd, c->smem_upd_f64,
-                                    c->smem_upd_f32, c->any_fp64, c->any_fp32, freeze_tol, c->d_resid_all, c->stream);
+        cudaError_t e = step_once(c, freeze_tol);
         if (e != cudaSuccess) return cuda_check(c, e, "fdlb_step launch");
     }
     return FDLB_OK;
@@ -706,4 +749,27 @@ extern "C" int fdlb_set_state(fdlb_ctx* c, int32_t inst, const void* host, size_
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.steps, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream), "state upload");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "state synchronize");
     return rc;
+}
+
+extern "C" int fdlb_profile(fdlb_ctx* c, int32_t on) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_profile: null context");
+    c->prof = on != 0;
+    for (int k = 0; k < KK_COUNT; ++k) c->nev[k] = 0;
+    return FDLB_OK;
+}
+
+extern "C" int fdlb_profile_read(fdlb_ctx* c, int32_t kind, double* total_ms, int64_t* launches) {
+    if (!c || kind < 0 || kind >= KK_COUNT) return fail(c, FDLB_EINVAL, "fdlb_profile_read: bad arguments");
+    int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "profile synchronize");
+    if (rc) return rc;
+    double tot = 0.0;
+    for (size_t j = 0; j + 1 < c->nev[kind]; j += 2) {
+        float ms = 0.0f;
+        rc = cuda_check(c, cudaEventElapsedTime(&ms, c->ev[kind][j], c->ev[kind][j + 1]), "profile elapsed");
+        if (rc) return rc;
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int64_t)(c->nev[kind] / 2);
+    return FDLB_OK;
 }

@@ -672,26 +672,19 @@ static cudaError_t set_smem(size_t smem64, size_t smem32) {
     return e;
 }
 
-cudaError_t launch_step(const Inst* d_inst, int count, const Work* d_mom, int n_mom, const Work* d_upd, int n_upd,
-                        size_t smem64, size_t smem32, bool f64, bool f32, double freeze_tol, double* d_resid_all,
-                        cudaStream_t s) {
+cudaError_t launch_nodal(const Inst* d_inst, int count, cudaStream_t s) {
+    k_nodal<<<count, 128, 0, s>>>(d_inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
+                          bool f64, bool f32, cudaStream_t s) {
     cudaError_t e = set_smem(smem64, smem32);
     if (e != cudaSuccess) return e;
     dim3 blk(TILE, UPD_WARPS);
-    for (int stage = 1; stage <= 3; ++stage) {
-        if (stage > 1) {
-            e = launch_moments(d_inst, d_mom, n_mom, stage - 1, f64, f32, s);
-            if (e != cudaSuccess) return e;
-        }
-        k_nodal<<<count, 128, 0, s>>>(d_inst);
-        if (f64) k_update<double, double><<<n_upd, blk, smem64, s>>>(d_inst, d_upd, stage);
-        if (f32) k_update<float, float><<<n_upd, blk, smem32, s>>>(d_inst, d_upd, stage);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    e = launch_moments(d_inst, d_mom, n_mom, 0, f64, f32, s);
-    if (e != cudaSuccess) return e;
-    return launch_resid(d_inst, count, -2, freeze_tol, d_resid_all, s);
+    if (f64) k_update<double, double><<<n_upd, blk, smem64, s>>>(d_inst, d_upd, stage);
+    if (f32) k_update<float, float><<<n_upd, blk, smem32, s>>>(d_inst, d_upd, stage);
+    return cudaGetLastError();
 }
 
 }  // namespace fdlb

@@ -20,10 +20,14 @@ cudaError_t launch_resid(const Inst* d_inst, int count, int anchor_inst, double 
 // Projected local equilibrium from the profile rows (n, u_x, u_y, T) of instance `inst` into F.
 cudaError_t launch_set_profiles(const Inst* d_inst, int inst, cudaStream_t s);
 
-// One full TVD-RK3 step of every ACTIVE instance, ending with the moments of the new state
-// and the residual/status pass.
-cudaError_t launch_step(const Inst* d_inst, int count, const Work* d_mom, int n_mom, const Work* d_upd, int n_upd,
-                        size_t smem64, size_t smem32, bool f64, bool f32, double freeze_tol, double* d_resid_all,
-                        cudaStream_t s);
+// Per-node closure (chi, Pr, tau, gradients, projection tables, wall densities).
+cudaError_t launch_nodal(const Inst* d_inst, int count, cudaStream_t s);
+
+// RK stage `stage` (1..3) update of every ACTIVE instance.
+cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
+                          bool f64, bool f32, cudaStream_t s);
+
+// Kernel classes for the optional event timing of fdlb_profile.
+enum KernelKind : int { KK_MOMENTS = 0, KK_NODAL = 1, KK_UPDATE = 2, KK_RESID = 3, KK_COUNT = 4 };
 
 }  // namespace fdlb

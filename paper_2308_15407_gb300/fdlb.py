@@ -99,6 +99,8 @@ def load() -> C.CDLL:
         "fdlb_get_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
         "fdlb_set_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
         "fdlb_quadrature": (C.c_int, [C.c_int32, C.c_int32, dp, dp]),
+        "fdlb_profile": (C.c_int, [vp, C.c_int32]),
+        "fdlb_profile_read": (C.c_int, [vp, C.c_int32, dp, lp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -215,6 +217,21 @@ class Solver:
         buf = C.create_string_buffer(nb)
         self._check(self.lib.fdlb_get_state(self.ctx, inst, buf, nb))
         return buf.raw
+
+    KERNEL_KINDS = ("moments", "nodal", "update", "resid")
+
+    def profile(self, on: bool):
+        """Start (clearing) or stop the per-kernel-class CUDA event timing."""
+        self._check(self.lib.fdlb_profile(self.ctx, int(bool(on))))
+
+    def profile_read(self) -> dict:
+        """{kind: (total_ms, launches)} of the recorded launches (synchronises)."""
+        out = {}
+        for j, name in enumerate(self.KERNEL_KINDS):
+            ms, n = C.c_double(), C.c_int64()
+            self._check(self.lib.fdlb_profile_read(self.ctx, j, C.byref(ms), C.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
 
     def set_state(self, inst: int, state: bytes):
         buf = C.create_string_buffer(state, len(state))
