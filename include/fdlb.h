@@ -163,6 +163,31 @@ int fdlb_set_state(fdlb_ctx* ctx, int32_t inst, const void* host, size_t bytes);
 int fdlb_profile(fdlb_ctx* ctx, int32_t on);
 int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 
+/* Largest scratch fdlb_step_noalloc can use (8 MiB): enough for one instance of e.g.
+ * nx = 400 with 16 x 6 x 6 velocities in FP64. */
+#define FDLB_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+
+/* Stepping without any device allocation, for callers that cannot call cudaMalloc (or any
+ * allocator): code running where allocation is forbidden or unsafe, e.g. inside a
+ * host-side callback of a framework that owns all device memory, a plug-in sandboxed
+ * from the allocator, or a real-time loop that must not trigger allocator
+ * synchronisation.  The paper has no counterpart; this is a library service.
+ *
+ * Advances ONE instance (params) by nsteps RK3 steps in place: dev_f (f_bytes bytes of
+ * device memory) holds its f in the layout described at the top of this file, i.e.
+ * K * ceil(nx/32)*32 values of double (FDLB_FP64) or float (FDLB_FP32_STORAGE) with
+ * K = 2 qx_half * T_c.  If dev_moments is not NULL it receives the 8 x nx moment rows of
+ * the result (as fdlb_moments, device memory).  All scratch lives in one static device
+ * array of FDLB_NOALLOC_SCRATCH_BYTES that every device loading the library holds until the
+ * process exits; instances that need more are rejected with FDLB_ENOMEM.  The array is
+ * shared by every call and keeps the last call's contents (each call rebuilds what it
+ * reads), so calls that overlap on the GPU race: serialise them.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Synchronises `stream`.
+ * Errors: FDLB_EINVAL (bad params or f_bytes), FDLB_ENOMEM, FDLB_ECUDA. */
+int fdlb_step_noalloc(const fdlb_params* params, void* dev_f, size_t f_bytes, int64_t nsteps,
+                      double* dev_moments, void* stream);
+
 /* Host-only: the library's own Gauss rules (for checking the tables; no GPU needed).
  * kind 0 = half-range Gauss-Hermite on [0, inf) (Sec. III A 2), kind 1 = full-range (App. A);
  * weights are normalised to the weight omega(p) = exp(-p^2/2)/sqrt(2 pi).  nodes/weights

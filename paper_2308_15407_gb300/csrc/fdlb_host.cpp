@@ -11,6 +11,7 @@
 //  * Grid mapping, time step, workspace layout, work lists, error handling.
 #include "fdlb_internal.h"
 #include "fdlb_launch.h"
+#include "fdlb_ctx_internal.h"
 #include "../../include/fdlb.h"
 
 #include <cuda_runtime.h>
@@ -773,3 +774,41 @@ extern "C" int fdlb_profile_read(fdlb_ctx* c, int32_t kind, double* total_ms, in
     if (launches) *launches = (int64_t)(c->nev[kind] / 2);
     return FDLB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// internal accessors (fdlb_ctx_internal.h)
+// ---------------------------------------------------------------------------
+namespace fdlb {
+
+int ctx_f_buffer(fdlb_ctx* c, int inst, void** f, size_t* bytes) {
+    if (!c || inst < 0 || inst >= c->count) return fail(c, FDLB_EINVAL, "internal: bad instance");
+    const Inst& I = c->inst[inst];
+    *f = I.f[0];
+    *bytes = (size_t)I.K * I.ld * (I.precision == FDLB_FP64 ? 8 : 4);
+    return FDLB_OK;
+}
+
+int ctx_reanchor(fdlb_ctx* c, int inst) {
+    if (!c || inst < 0 || inst >= c->count) return fail(c, FDLB_EINVAL, "internal: bad instance");
+    static const int active = FDLB_ACTIVE;
+    const Inst& I = c->inst[inst];
+    int rc = cuda_check(c, cudaMemcpyAsync(I.status, &active, sizeof(int), cudaMemcpyHostToDevice, c->stream), "status reset");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, c->count, inst, 0.0, c->d_resid_all, c->stream), "residual kernel");
+    return rc;
+}
+
+int ctx_moment_rows(fdlb_ctx* c, int inst, const double** rows, int* ld, int* nx) {
+    if (!c || inst < 0 || inst >= c->count) return fail(c, FDLB_EINVAL, "internal: bad instance");
+    const Inst& I = c->inst[inst];
+    *rows = I.node;
+    *ld = I.ld;
+    *nx = I.N;
+    return FDLB_OK;
+}
+
+cudaStream_t ctx_stream(fdlb_ctx* c) { return c->stream; }
+
+void set_global_error(const std::string& msg) { g_err = msg; }
+
+}  // namespace fdlb

@@ -99,6 +99,7 @@ def load() -> C.CDLL:
         "fdlb_get_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
         "fdlb_set_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
         "fdlb_quadrature": (C.c_int, [C.c_int32, C.c_int32, dp, dp]),
+        "fdlb_step_noalloc": (C.c_int, [P, vp, C.c_size_t, C.c_int64, dp, vp]),
         "fdlb_profile": (C.c_int, [vp, C.c_int32]),
         "fdlb_profile_read": (C.c_int, [vp, C.c_int32, dp, lp]),
     }
@@ -129,6 +130,21 @@ def quadrature(kind: str, q: int):
     if rc != FDLB_OK:
         raise FdlbError(rc, lib.fdlb_last_error(None).decode())
     return x, w
+
+
+def step_noalloc(params: Params, f_dev, nsteps: int, moments_dev=None, stream=None) -> None:
+    """fdlb_step_noalloc: advance one instance whose f lives in the caller's device tensor
+    f_dev (in place), with no device allocation by the library; moments_dev (float64 device
+    tensor of 8*nx) receives the moment rows."""
+    import torch
+    lib = load()
+    c = params.to_c()
+    st = stream if stream is not None else torch.cuda.current_stream(f_dev.device)
+    mp = C.cast(C.c_void_p(moments_dev.data_ptr()), C.POINTER(C.c_double)) if moments_dev is not None else None
+    rc = lib.fdlb_step_noalloc(C.byref(c), C.c_void_p(f_dev.data_ptr()), f_dev.numel() * f_dev.element_size(),
+                               int(nsteps), mp, C.c_void_p(st.cuda_stream))
+    if rc != FDLB_OK:
+        raise FdlbError(rc, lib.fdlb_last_error(None).decode())
 
 
 def workspace_bytes(params) -> int:
