@@ -38,7 +38,8 @@ struct fdlb_ctx {
     Inst* d_inst = nullptr;
     Work* d_mom = nullptr;
     Work* d_upd = nullptr;
-    int n_mom = 0, n_upd = 0;
+    Work* d_nod = nullptr;
+    int n_mom = 0, n_upd = 0, n_nod = 0, qmax = 1;
     int* d_status_all = nullptr;      // count ints (Inst::status points here)
     long long* d_steps_all = nullptr;
     double* d_resid_all = nullptr;    // count doubles (misc[M_RESID] copies)
@@ -83,7 +84,7 @@ static cudaError_t step_once(fdlb_ctx* c, double freeze_tol) {
     for (int stage = 1; stage <= 3; ++stage) {
         if (stage > 1)
             guard(KK_MOMENTS, [&] { return launch_moments(c->d_inst, c->d_mom, c->n_mom, stage - 1, c->any_fp64, c->any_fp32, c->stream); });
-        guard(KK_NODAL, [&] { return launch_nodal(c->d_inst, c->count, c->stream); });
+        guard(KK_NODAL, [&] { return launch_nodal(c->d_inst, c->d_nod, c->n_nod, c->qmax, c->stream); });
         guard(KK_UPDATE, [&] { return launch_update(c->d_inst, c->d_upd, c->n_upd, stage, c->smem_upd_f64, c->smem_upd_f32,
                                                     c->any_fp64, c->any_fp32, c->stream); });
     }
@@ -309,7 +310,7 @@ int validate(const fdlb_params& p, std::string& why) {
 
 // Byte layout of one instance inside the workspace.
 struct Layout {
-    size_t tables = 0, fbuf = 0, node = 0, tab = 0, misc = 0, total = 0;
+    size_t tables = 0, fbuf = 0, node = 0, tab = 0, tab32 = 0, misc = 0, total = 0;
     int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0;
 };
 
@@ -336,30 +337,35 @@ Layout layout_of(const fdlb_params& p) {
     add(p.nx); add(p.nx); add(21);
     add(L.K); add(L.K);
     add(QYMAX + 2); add(QYMAX + 2);
+    auto add32 = [&](size_t n) { nd += al256(n * 4) / 8; };
+    add(6 * L.Tc); add32(6 * L.Tc); add32(6 * L.Tc);
+    if (p.precision == FDLB_FP32_STORAGE) { add32(2 * Q); add32(p.nx); add32(QYMAX * QYMAX); add32(L.K); add32(L.K); }
     L.tables = nd * 8;
     const size_t es = p.precision == FDLB_FP64 ? 8 : 4;
     L.fbuf = al256((size_t)L.K * L.ld * es);
     L.node = al256((size_t)NROWS * L.ld * 8);
     L.tab = al256((size_t)L.ntab * L.ld * 8);
     L.misc = al256(8 * 8);
-    L.total = L.tables + 3 * L.fbuf + L.node + L.tab + L.misc;
+    L.tab32 = p.precision == FDLB_FP32_STORAGE ? al256((size_t)L.ntab * L.ld * 4) : 0;
+    L.total = L.tables + 3 * L.fbuf + L.node + L.tab + L.tab32 + L.misc;
     return L;
 }
 
-size_t global_bytes(int count, int n_mom, int n_upd) {
-    return al256(sizeof(Inst) * count) + al256(sizeof(Work) * n_mom) + al256(sizeof(Work) * n_upd) +
+size_t global_bytes(int count, int n_mom, int n_upd, int n_nod) {
+    return al256(sizeof(Inst) * count) + al256(sizeof(Work) * n_mom) + al256(sizeof(Work) * n_upd) + al256(sizeof(Work) * n_nod) +
            al256(sizeof(int) * count) + al256(sizeof(long long) * count) + al256(sizeof(double) * count);
 }
 
 const int KC = 32;   // velocities per update work item
 
-void count_work(const std::vector<fdlb_params>& p, int& n_mom, int& n_upd) {
-    n_mom = n_upd = 0;
+void count_work(const std::vector<fdlb_params>& p, int& n_mom, int& n_upd, int& n_nod) {
+    n_mom = n_upd = n_nod = 0;
     for (auto& q : p) {
         Layout L = layout_of(q);
         int tiles = (q.nx + TILE - 1) / TILE;
         n_mom += tiles;
         n_upd += tiles * ((L.K + KC - 1) / KC);
+        n_nod += (q.nx + NOD_WARPS - 1) / NOD_WARPS;
     }
 }
 
@@ -379,9 +385,9 @@ extern "C" size_t fdlb_workspace_bytes(const fdlb_params* params, int32_t count)
         std::string why;
         if (validate(p[i], why) != FDLB_OK) { g_err = "instance " + std::to_string(i) + ": " + why; return 0; }
     }
-    int n_mom, n_upd;
-    count_work(p, n_mom, n_upd);
-    size_t tot = global_bytes(count, n_mom, n_upd);
+    int n_mom, n_upd, n_nod;
+    count_work(p, n_mom, n_upd, n_nod);
+    size_t tot = global_bytes(count, n_mom, n_upd, n_nod);
     for (auto& q : p) tot += layout_of(q).total;
     return tot;
 }
@@ -399,21 +405,23 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     c->prm.assign(params, params + count);
     c->stream = reinterpret_cast<cudaStream_t>(stream);
 
-    int n_mom, n_upd;
-    count_work(c->prm, n_mom, n_upd);
+    int n_mom, n_upd, n_nod;
+    count_work(c->prm, n_mom, n_upd, n_nod);
     c->n_mom = n_mom;
     c->n_upd = n_upd;
+    c->n_nod = n_nod;
     char* base = reinterpret_cast<char*>(dev_workspace);
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base + off; off += al256(bytes); return p; };
     c->d_inst = reinterpret_cast<Inst*>(take(sizeof(Inst) * count));
     c->d_mom = reinterpret_cast<Work*>(take(sizeof(Work) * n_mom));
     c->d_upd = reinterpret_cast<Work*>(take(sizeof(Work) * n_upd));
+    c->d_nod = reinterpret_cast<Work*>(take(sizeof(Work) * n_nod));
     c->d_status_all = reinterpret_cast<int*>(take(sizeof(int) * count));
     c->d_steps_all = reinterpret_cast<long long*>(take(sizeof(long long) * count));
     c->d_resid_all = reinterpret_cast<double*>(take(sizeof(double) * count));
 
-    std::vector<Work> wm, wu;
+    std::vector<Work> wm, wu, wn;
     std::vector<char> staging;        // host image of all table regions
     std::vector<std::pair<size_t, size_t>> regions;   // (offset, size) of table regions
     size_t max_smem64 = 0, max_smem32 = 0;
@@ -442,6 +450,12 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             double* h = img.data() + pos;
             *dst = reinterpret_cast<const double*>(base + tab_off + pos * 8);
             pos += al256(n * 8) / 8;
+            return h;
+        };
+        auto put32 = [&](const float** dst, size_t n) -> float* {
+            float* h = reinterpret_cast<float*>(img.data() + pos);
+            *dst = reinterpret_cast<const float*>(base + tab_off + pos * 8);
+            pos += al256(n * 4) / 8;
             return h;
         };
         auto putw = [&](double** dst, size_t n) -> double* {
@@ -559,6 +573,38 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             double* hib = put(&I.fisq, QYMAX + 2);
             for (int l = 0; l < QYMAX + 2; ++l) { hb[l] = std::sqrt((double)l); hib[l] = l ? 1.0 / std::sqrt((double)l) : 0.0; }
         }
+        {
+            // transverse weights of the factorised moment sums, and their float head/tail split
+            const double* hm = reinterpret_cast<const double*>(img.data()) + ((const char*)I.tmt - (base + tab_off)) / 8;
+            const double* hy = reinterpret_cast<const double*>(img.data()) + ((const char*)I.tpy - (base + tab_off)) / 8;
+            const double* he = reinterpret_cast<const double*>(img.data()) + ((const char*)I.tet - (base + tab_off)) / 8;
+            double* tw = put(&I.tw, 6 * L.Tc);
+            float* twh = put32(&I.twh, 6 * L.Tc);
+            float* twl = put32(&I.twl, 6 * L.Tc);
+            for (int t = 0; t < L.Tc; ++t) {
+                const double w6[6] = {hm[t], hm[t] * hy[t], hm[t] * hy[t] * hy[t], hm[t] * hy[t] * hy[t] * hy[t], he[t], he[t] * hy[t]};
+                for (int j = 0; j < 6; ++j) {
+                    tw[j * L.Tc + t] = w6[j];
+                    twh[j * L.Tc + t] = (float)w6[j];
+                    twl[j * L.Tc + t] = (float)(w6[j] - (double)(float)w6[j]);
+                }
+            }
+        }
+        if (p.precision == FDLB_FP32_STORAGE) {
+            const double* img0 = reinterpret_cast<const double*>(img.data());
+            auto host_of = [&](const double* dev) { return img0 + ((const char*)dev - (base + tab_off)) / 8; };
+            float* h = put32(&I.px32, 2 * Q);
+            for (int k = 0; k < 2 * Q; ++k) h[k] = (float)host_of(I.px)[k];
+            h = put32(&I.xpinv32, N);
+            for (int i = 0; i < N; ++i) h[i] = (float)host_of(I.xpinv)[i];
+            h = put32(&I.Ky32, QYMAX * QYMAX);
+            for (int k = 0; k < QYMAX * QYMAX; ++k) h[k] = (float)host_of(I.Ky)[k];
+            const float* g32;
+            put32(&g32, L.K);
+            I.gL32 = const_cast<float*>(g32);
+            put32(&g32, L.K);
+            I.gR32 = const_cast<float*>(g32);
+        }
         if (pos * 8 != L.tables) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: table layout mismatch"); }
         regions.push_back({tab_off, L.tables});
         {
@@ -571,6 +617,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         for (int b = 0; b < 3; ++b) I.f[b] = take(L.fbuf);
         I.node = reinterpret_cast<double*>(take(L.node));
         I.tab = reinterpret_cast<double*>(take(L.tab));
+        I.tab32 = L.tab32 ? reinterpret_cast<float*>(take(L.tab32)) : nullptr;
         I.misc = reinterpret_cast<double*>(take(L.misc));
         I.status = c->d_status_all + ii;
         I.steps = c->d_steps_all + ii;
@@ -581,6 +628,8 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             wm.push_back({ii, t * TILE, 0, L.K});
             for (int k0 = 0; k0 < L.K; k0 += KC) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + KC)});
         }
+        for (int i0 = 0; i0 < N; i0 += NOD_WARPS) wn.push_back({ii, i0, 0, 0});
+        c->qmax = std::max(c->qmax, Q);
         size_t sm = (size_t)L.ntab * TILE;
         if (p.precision == FDLB_FP64) max_smem64 = std::max(max_smem64, sm * 8), c->any_fp64 = true;
         else max_smem32 = std::max(max_smem32, sm * 4), c->any_fp32 = true;
@@ -601,6 +650,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     rc = cuda_check(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s), "upload descriptors");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_mom, wm.data(), sizeof(Work) * n_mom, cudaMemcpyHostToDevice, s), "upload work");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_upd, wu.data(), sizeof(Work) * n_upd, cudaMemcpyHostToDevice, s), "upload work");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_nod, wn.data(), sizeof(Work) * n_nod, cudaMemcpyHostToDevice, s), "upload work");
     if (!rc) rc = cuda_check(c, launch_setup(c->d_inst, count, s), "setup kernel");
     if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, n_mom, 0, c->any_fp64, c->any_fp32, s), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, count, 1, 0.0, c->d_resid_all, s), "residual kernel");

@@ -14,6 +14,7 @@ constexpr int MX = 16;          // auxiliary half-range rule used for the x proj
 constexpr int MYMAX = 8;        // auxiliary full-range rule (exact: 2M > Q + 2)
 constexpr int NTERMS = 13;      // monomials of f^S + tau J1
 constexpr int TILE = 32;        // nodes per tile (one warp lane per node)
+constexpr int NOD_WARPS = 4;    // nodes per k_nodal block (one warp per node)
 
 enum Form : int { FORM_UNREDUCED = 0, FORM_REDUCED2D = 1, FORM_REDUCED1D = 2 };
 
@@ -61,10 +62,20 @@ struct Inst {
     const double* xpinv;       // [N] 1/(x'(s_i) ds)
     const double* dxw;         // [N] x'(s_i) ds
     const double* gst;         // [3*7] gradient weights (in s) for nodes 0,1,2 on nodes 0..6
+    const double* tw;          // [6*Tc] transverse moment weights mt, mt py, mt py^2, mt py^3, et, et py
+    const float* twh;          // [6*Tc] float head of tw
+    const float* twl;          // [6*Tc] float tail of tw (tw - twh)
     const double* fsq;         // [QYMAX+2] sqrt(l)
     const double* fisq;        // [QYMAX+2] 1/sqrt(l) (l >= 1)
     double* gL;                // [K] unit-density wall Maxwellians
     double* gR;                // [K]
+    // FP32 copies read by the update kernel of FP32-storage instances (null otherwise)
+    const float* px32;         // [2Q]
+    const float* xpinv32;      // [N]
+    const float* Ky32;         // [Qy*Qy]
+    float* gL32;               // [K]
+    float* gR32;               // [K]
+    float* tab32;              // [ntab*ld]
     void* f[3];                // RK buffers F, A, B; each K*ld elements of the storage type
     double* node;              // [NROWS*ld]
     double* tab;               // [ntab*ld] projection table (see below)

@@ -195,6 +195,11 @@ __global__ void k_setup(Inst* insts) {
     if (threadIdx.x == 0) wall_maxwellian(I, I.U_L, I.T_L, I.gL);
     if (threadIdx.x == 32) wall_maxwellian(I, I.U_R, I.T_R, I.gR);
     __syncthreads();
+    if (I.gL32)
+        for (int k = threadIdx.x; k < I.K; k += blockDim.x) {
+            I.gL32[k] = (float)I.gL[k];
+            I.gR32[k] = (float)I.gR[k];
+        }
     if (threadIdx.x == 0) {
         const int Q = I.Q, Tc = I.Tc;
         double inL = 0.0, inR = 0.0;
@@ -257,44 +262,88 @@ __global__ void k_profiles(Inst* insts, int inst) {
 // moments
 // ---------------------------------------------------------------------------
 constexpr int MOM_WARPS = 8;
-constexpr int NSUM = 15;
+constexpr int NSUM = 14;
+constexpr int NTW = 6;     // transverse weights: mt, mt py, mt py^2, mt py^3, et, et py
 
+// Inner (transverse) running sum of w(t) f over t.  FP64 storage: an FP64 FMA.  FP32
+// storage: an unevaluated pair hi + lo of floats (error-free product of f with the float
+// head of w, the tail of w applied in float, TwoSum accumulation), ~1e-13 relative.
+template <typename S>
+struct InnerSum;
+
+template <>
+struct InnerSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double f, double w, float, float) { s = fma(w, f, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct InnerSum<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float f, double, float wh, float wl) {
+        const float p = f * wh;
+        float e = fmaf(f, wh, -p);
+        e = fmaf(f, wl, e);
+        const float t = hi + p;
+        const float bb = t - hi;
+        const float err = (hi - (t - bb)) + (p - bb);
+        hi = t;
+        lo += err + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Per node: the 14 raw sums over all velocities, factorised as sum_kx px^a (sum_t w_j(t) f).
 template <typename S>
 __global__ void __launch_bounds__(TILE * MOM_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
+    __shared__ double red[NSUM][MOM_WARPS][TILE];
+    __shared__ double sw[NTW][TCMAX];
+    __shared__ float swh[NTW][TCMAX], swl[NTW][TCMAX];
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE) return;
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     const int lane = threadIdx.x, g = threadIdx.y;
     const int i = w.i0 + lane;
-    const int N = I.N, ld = I.ld, Tc = I.Tc, K = I.K, Q = I.Q;
-    const bool valid = i < N;
+    const int ld = I.ld, Tc = I.Tc, Q = I.Q;
+    const bool valid = i < I.N;
+    for (int o = g * TILE + lane; o < NTW * Tc; o += TILE * MOM_WARPS) {
+        const int j = o / Tc, t = o - j * Tc;
+        sw[j][t] = I.tw[o];
+        swh[j][t] = I.twh[o];
+        swl[j][t] = I.twl[o];
+    }
+    __syncthreads();
     const S* f = static_cast<const S*>(I.f[buf]);
     double acc[NSUM];
 #pragma unroll
     for (int j = 0; j < NSUM; ++j) acc[j] = 0.0;
-    // s0 sneg spos sy sxx sxy syy se sxxx sxyy sxxy syyy sxe sye (14 used)
-    for (int k = g; k < K; k += MOM_WARPS) {
-        const int kx = k / Tc, t = k - kx * Tc;
-        const double fv = valid ? (double)f[(size_t)k * ld + i] : 0.0;
-        const double p = I.px[kx], py = I.tpy[t], mt = I.tmt[t], et = I.tet[t];
-        const double mf = mt * fv, ef = et * fv;
-        const double mfp = mf * p, mfy = mf * py;
-        acc[0] += mf;
-        if (kx >= Q) acc[1] += mfp; else acc[2] += mfp;
-        acc[3] += mfy;
-        acc[4] = fma(mfp, p, acc[4]);
-        acc[5] = fma(mfp, py, acc[5]);
-        acc[6] = fma(mfy, py, acc[6]);
-        acc[7] += ef;
-        acc[8] = fma(mfp * p, p, acc[8]);
-        acc[9] = fma(mfp * py, py, acc[9]);
-        acc[10] = fma(mfp * p, py, acc[10]);
-        acc[11] = fma(mfy * py, py, acc[11]);
-        acc[12] = fma(ef, p, acc[12]);
-        acc[13] = fma(ef, py, acc[13]);
+    for (int kx = g; kx < 2 * Q; kx += MOM_WARPS) {
+        InnerSum<S> a[NTW];
+        const S* row = f + (size_t)kx * Tc * ld + (valid ? i : 0);
+        for (int t = 0; t < Tc; ++t) {
+            const S fv = valid ? row[(size_t)t * ld] : (S)0;
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) a[j].add(fv, sw[j][t], swh[j][t], swl[j][t]);
+        }
+        const double S0 = a[0].value(), S1 = a[1].value(), S2 = a[2].value(), S3 = a[3].value();
+        const double S4 = a[4].value(), S5 = a[5].value();
+        const double p = I.px[kx], p2 = p * p, p3 = p2 * p;
+        acc[0] += S0;
+        if (kx >= Q) acc[1] = fma(p, S0, acc[1]); else acc[2] = fma(p, S0, acc[2]);
+        acc[3] += S1;
+        acc[4] = fma(p2, S0, acc[4]);
+        acc[5] = fma(p, S1, acc[5]);
+        acc[6] += S2;
+        acc[7] += S4;
+        acc[8] = fma(p3, S0, acc[8]);
+        acc[9] = fma(p, S2, acc[9]);
+        acc[10] = fma(p2, S1, acc[10]);
+        acc[11] += S3;
+        acc[12] = fma(p, S4, acc[12]);
+        acc[13] += S5;
     }
-    __shared__ double red[NSUM][MOM_WARPS][TILE];
 #pragma unroll
     for (int j = 0; j < NSUM; ++j) red[j][g][lane] = acc[j];
     __syncthreads();
@@ -306,6 +355,7 @@ __global__ void __launch_bounds__(TILE * MOM_WARPS) k_moments(const Inst* __rest
         for (int q = 0; q < MOM_WARPS; ++q) v += red[j][q][lane];
         s[j] = v;
     }
+    // s: 0 n, 1 sneg, 2 spos, 3 sy, 4 sxx, 5 sxy, 6 syy, 7 se, 8 sxxx, 9 sxyy, 10 sxxy, 11 syyy, 12 sxe, 13 sye
     const double n = s[0], sx = s[1] + s[2];
     const double ux = sx / n, uy = s[3] / n;
     const double Pxx = s[4] - n * ux * ux, Pxy = s[5] - n * ux * uy, Pyy = s[6] - n * uy * uy;
@@ -331,70 +381,226 @@ __global__ void __launch_bounds__(TILE * MOM_WARPS) k_moments(const Inst* __rest
 }
 
 // ---------------------------------------------------------------------------
-// per-node closure and projection tables
+// per-node closure and projection tables: one warp per node
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_nodal(const Inst* __restrict__ insts) {
-    const Inst& I = insts[blockIdx.x];
+// Shared doubles per warp: scalars (32) | partial products | G (8Q) | Py (4 QYMAX) | Pz (3 QZMAX).
+__host__ __device__ inline int nodal_partials(int Q) { return 128 * Q > 448 ? 128 * Q : 448; }
+__host__ __device__ inline int nodal_warp_doubles(int Q) { return 32 + nodal_partials(Q) + 8 * Q + 4 * QYMAX + 3 * QZMAX; }
+
+__global__ void __launch_bounds__(32 * NOD_WARPS) k_nodal(const Inst* __restrict__ insts, const Work* __restrict__ work, int wdoubles) {
+    extern __shared__ __align__(16) double nsm[];
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = w.i0 + wid;
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc;
+    if (i >= N) return;                 // whole warp; only warp-level synchronisation below
+    double* sc = nsm + wid * wdoubles;
+    double* Gp = sc + 32;
+    double* Gs = Gp + nodal_partials(Q);
+    double* Py = Gs + 8 * Q;
+    double* Pz = Py + 4 * QYMAX;
     const double* nd = I.node;
-    if (threadIdx.x == 0) {
-        // zero net mass flux through each wall (Sec. III B): outgoing wall-face flux is the
+    if (i == 0 && lane == 0) {
+        // zero net mass flux through each wall (Sec. III B): the outgoing wall-face flux is the
         // quadratic reconstruction (11 f_1 - 7 f_2 + 2 f_3)/6 of the outgoing populations.
         const double oL = (11.0 * nd[R_SNEG * ld + 0] - 7.0 * nd[R_SNEG * ld + 1] + 2.0 * nd[R_SNEG * ld + 2]) / 6.0;
         const double oR = (11.0 * nd[R_SPOS * ld + N - 1] - 7.0 * nd[R_SPOS * ld + N - 2] + 2.0 * nd[R_SPOS * ld + N - 3]) / 6.0;
         I.misc[M_NWL] = -oL / I.misc[M_INL];
         I.misc[M_NWR] = -oR / I.misc[M_INR];
     }
-    const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
-    const double k_mu = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
-    const double k_pn = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
-    const double k_pd = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * CUDART_PI));
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double gn = 0.0, gc = 0.0, gT = 0.0, gux = 0.0, guy = 0.0;
-        for (int j = 0; j < 7; ++j) {
-            int idx;
-            double wj;
-            if (i < 3) { idx = j; wj = I.gst[i * 7 + j]; }
-            else if (i > N - 4) { const int m = N - 1 - i; idx = N - 1 - j; wj = -I.gst[m * 7 + j]; }
-            else { idx = i - 3 + j; wj = cen[j]; }
-            if (wj == 0.0) continue;
-            const double nj = nd[R_N * ld + idx], Tj = nd[R_T * ld + idx];
-            gn = fma(wj, log(nj), gn);
-            gc = fma(wj, log(chi_cs(I.eta0 * nj)), gc);
-            gT = fma(wj, log(Tj), gT);
-            gux = fma(wj, nd[R_UX * ld + idx], gux);
-            guy = fma(wj, nd[R_UY * ld + idx], guy);
+    // ---- gradients (Sec. III B 3): lane j < 7 takes stencil point j
+    double gn = 0.0, gc = 0.0, gT = 0.0, gux = 0.0, guy = 0.0;
+    if (lane < 7) {
+        int idx;
+        double wj;
+        if (i < 3) { idx = lane; wj = I.gst[i * 7 + lane]; }
+        else if (i > N - 4) { const int m = N - 1 - i; idx = N - 1 - lane; wj = -I.gst[m * 7 + lane]; }
+        else {
+            const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
+            idx = i - 3 + lane;
+            wj = cen[lane];
         }
+        if (wj != 0.0) {
+            const double nj = nd[R_N * ld + idx], Tj = nd[R_T * ld + idx];
+            gn = wj * log(nj);
+            gc = wj * log(chi_cs(I.eta0 * nj));
+            gT = wj * log(Tj);
+            gux = wj * nd[R_UX * ld + idx];
+            guy = wj * nd[R_UY * ld + idx];
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        gn += __shfl_xor_sync(0xffffffffu, gn, o);
+        gc += __shfl_xor_sync(0xffffffffu, gc, o);
+        gT += __shfl_xor_sync(0xffffffffu, gT, o);
+        gux += __shfl_xor_sync(0xffffffffu, gux, o);
+        guy += __shfl_xor_sync(0xffffffffu, guy, o);
+    }
+    // ---- closure and the 13 coefficients (lane 0)
+    if (lane == 0) {
+        const double k_mu = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
+        const double k_pd = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * CUDART_PI));
         const double xi = I.xpinv[i];
         const double Gr = (2.0 * gn + gc + gT) * xi, Br = gT * xi, Ur = gux * xi, Vr = guy * xi;
         const double n = nd[R_N * ld + i], ux = nd[R_UX * ld + i], uy = nd[R_UY * ld + i], T = nd[R_T * ld + i];
         const double qx = nd[R_QX * ld + i], qy = nd[R_QY * ld + i];
         const double eta = I.eta0 * n, chi = chi_cs(eta), br = 4.0 * eta, brc = br * chi;
-        const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_pn * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
+        const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_mu * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
         const double mu = I.mu0c * sqrt(T) * (1.0 / chi + 0.8 * br + k_mu * br * br * chi);
         const double tau = mu / (n * T);
-        // f^S + tau J1 = n g(xi) * sum_j c_j xi^(a_j, b_j, c_j)
+        // f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j)  (Sec. II A, Eq. j1)
         const double A = (1.0 - Pr) / (5.0 * n * T * T), W = -tau * brc, iT = 1.0 / T;
-        double c[NTERMS];
-        c[0] = 1.0 - W * Ur;
-        c[1] = -5.0 * A * qx + W * (Gr - 1.5 * Br);
-        c[2] = -5.0 * A * qy;
-        c[3] = W * 0.6 * Ur * iT;
-        c[4] = W * 0.2 * Ur * iT;
-        c[5] = c[4];
-        c[6] = I.j1_shear ? W * 0.4 * Vr * iT : 0.0;
-        c[7] = A * qx * iT + W * 0.3 * Br * iT;
-        c[8] = c[7];
-        c[9] = c[7];
-        c[10] = A * qy * iT;
-        c[11] = c[10];
-        c[12] = c[10];
-        double* col = I.tab + i;
-        proj_x(I, ux, T, 0, col, ld);
-        proj_x(I, ux, T, 1, col, ld);
-        build_Y(I, c, uy, T, n, col + 8 * Q * ld, ld);
-        col[(8 * Q + 4 * Tc) * ld] = 1.0 / tau;
+        sc[0] = 1.0 - W * Ur;
+        sc[1] = -5.0 * A * qx + W * (Gr - 1.5 * Br);
+        sc[2] = -5.0 * A * qy;
+        sc[3] = W * 0.6 * Ur * iT;
+        sc[4] = W * 0.2 * Ur * iT;
+        sc[5] = sc[4];
+        sc[6] = I.j1_shear ? W * 0.4 * Vr * iT : 0.0;
+        sc[7] = A * qx * iT + W * 0.3 * Br * iT;
+        sc[8] = sc[7];
+        sc[9] = sc[7];
+        sc[10] = A * qy * iT;
+        sc[11] = sc[10];
+        sc[12] = sc[10];
+        sc[13] = T;
+        sc[14] = ux;
+        sc[15] = uy;
+        sc[16] = n;
+        sc[17] = 1.0 / tau;
+    }
+    __syncwarp();
+    // ---- half-range x projection (Sec. III A 2): lane = half * 16 + aux point
+    {
+        const int half = lane >> 4, m = lane & 15;
+        const double T = sc[13], uu = half ? -sc[14] : sc[14];
+        const double sT = sqrt(T), v = uu / sT;
+        const double q = I.xq[m], x = sT * q;
+        const double E = I.xw[m] * exp(fma(q, v, -0.5 * v * v));
+        const double y = x - uu, e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+        double hm = 0.0, h = I.x_h0;
+        for (int l = 0; l < Q; ++l) {
+            Gp[(0 * Q + l) * 32 + lane] = E * h;
+            Gp[(1 * Q + l) * 32 + lane] = e1 * h;
+            Gp[(2 * Q + l) * 32 + lane] = e2 * h;
+            Gp[(3 * Q + l) * 32 + lane] = e3 * h;
+            const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
+            hm = h;
+            h = hn;
+        }
+    }
+    __syncwarp();
+    for (int o = lane; o < 8 * Q; o += 32) {
+        const int hf = o / (4 * Q), r = o - hf * 4 * Q;            // r = a Q + l
+        const double* src = Gp + r * 32 + hf * 16;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) s += src[m];
+        Gs[o] = s;
+    }
+    __syncwarp();
+    for (int o = lane; o < 8 * Q; o += 32) {
+        const int a = o / (2 * Q), kx = o - a * 2 * Q, hf = kx >= Q ? 1 : 0, k = kx - hf * Q;
+        const double* gg = Gs + hf * 4 * Q + a * Q;
+        double s = 0.0;
+        for (int l = 0; l < Q; ++l) s = fma(I.xH[l * Q + k], gg[l], s);
+        if (hf && (a & 1)) s = -s;
+        const size_t r = (size_t)(a * 2 * Q + kx) * ld + i;
+        I.tab[r] = s;
+        if (I.tab32) I.tab32[r] = (float)s;
+    }
+    // ---- full-range y and z projections (App. A)
+    if (I.form != FORM_REDUCED1D) {
+        __syncwarp();
+        const double T = sc[13], sT = sqrt(T);
+        const int Qy = I.Qy, Qz = I.Qz;
+        if (lane < I.My) {
+            const double y = sT * I.yq[lane], x = sc[15] + y, E = I.yw[lane];
+            const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+            double hm = 0.0, h = 1.0;
+            for (int l = 0; l < Qy; ++l) {
+                Gp[(0 * QYMAX + l) * 8 + lane] = E * h;
+                Gp[(1 * QYMAX + l) * 8 + lane] = e1 * h;
+                Gp[(2 * QYMAX + l) * 8 + lane] = e2 * h;
+                Gp[(3 * QYMAX + l) * 8 + lane] = e3 * h;
+                const double hn = (x * h - I.fsq[l] * hm) * I.fisq[l + 1];
+                hm = h;
+                h = hn;
+            }
+        }
+        if (I.form == FORM_UNREDUCED && lane >= 16 && lane < 16 + I.Mz) {
+            const int m = lane - 16;
+            const double y = sT * I.zq[m], E = I.zw[m];
+            const double e1 = E * y, e2 = e1 * y;
+            double hm = 0.0, h = 1.0;
+            for (int l = 0; l < Qz; ++l) {
+                Gp[256 + (0 * QZMAX + l) * 8 + m] = E * h;
+                Gp[256 + (1 * QZMAX + l) * 8 + m] = e1 * h;
+                Gp[256 + (2 * QZMAX + l) * 8 + m] = e2 * h;
+                const double hn = (y * h - I.fsq[l] * hm) * I.fisq[l + 1];
+                hm = h;
+                h = hn;
+            }
+        }
+        __syncwarp();
+        for (int o = lane; o < 4 * Qy; o += 32) {
+            const int a = o / Qy, k = o - a * Qy;
+            double s = 0.0;
+            for (int l = 0; l < Qy; ++l) {
+                double t = 0.0;
+                for (int m = 0; m < I.My; ++m) t += Gp[(a * QYMAX + l) * 8 + m];
+                s = fma(I.yH[l * Qy + k], t, s);
+            }
+            Py[a * QYMAX + k] = s;
+        }
+        if (I.form == FORM_UNREDUCED)
+            for (int o = lane; o < 3 * Qz; o += 32) {
+                const int a = o / Qz, k = o - a * Qz;
+                double s = 0.0;
+                for (int l = 0; l < Qz; ++l) {
+                    double t = 0.0;
+                    for (int m = 0; m < I.Mz; ++m) t += Gp[256 + (a * QZMAX + l) * 8 + m];
+                    s = fma(I.zH[l * Qz + k], t, s);
+                }
+                Pz[a * QZMAX + k] = s;
+            }
+        __syncwarp();
+    }
+    // ---- transverse factors n Y[a][t]
+    {
+        const double n = sc[16], T = sc[13];
+        const int Qz = I.Qz;
+        for (int o = lane; o < 4 * Tc; o += 32) {
+            const int a = o / Tc, t = o - a * Tc;
+            double s = 0.0;
+            for (int j = 0; j < NTERMS; ++j) {
+                if (c_mono[j][0] != a) continue;
+                const int b = c_mono[j][1], cc = c_mono[j][2];
+                double e;
+                if (I.form == FORM_UNREDUCED) {
+                    const int ky = t / Qz, kz = t - ky * Qz;
+                    e = Py[b * QYMAX + ky] * Pz[cc * QZMAX + kz];
+                } else if (I.form == FORM_REDUCED2D) {
+                    const int ky = t >> 1, slot = t & 1;
+                    e = Py[b * QYMAX + ky] * (slot == 0 ? gmom(cc, T) : gmom(cc + 2, T));
+                } else {
+                    e = t == 0 ? gmom(b, T) * gmom(cc, T) : gmom(b + 2, T) * gmom(cc, T) + gmom(b, T) * gmom(cc + 2, T);
+                }
+                s = fma(sc[j], e, s);
+            }
+            s *= n;
+            const size_t r = (size_t)(8 * Q + a * Tc + t) * ld + i;
+            I.tab[r] = s;
+            if (I.tab32) I.tab32[r] = (float)s;
+        }
+    }
+    if (lane == 0) {
+        const size_t r = (size_t)(8 * Q + 4 * Tc) * ld + i;
+        I.tab[r] = sc[17];
+        if (I.tab32) I.tab32[r] = (float)sc[17];
     }
 }
 
@@ -543,6 +749,28 @@ __device__ __forceinline__ float weno_face(float a, float b, float c, float d, f
 
 constexpr int UPD_WARPS = 8;
 
+// Tables read by the update kernel in its compute type (FP32 copies for FP32 storage).
+template <typename C>
+struct Tabs;
+template <>
+struct Tabs<double> {
+    __device__ static const double* tab(const Inst& I) { return I.tab; }
+    __device__ static const double* px(const Inst& I) { return I.px; }
+    __device__ static const double* gL(const Inst& I) { return I.gL; }
+    __device__ static const double* gR(const Inst& I) { return I.gR; }
+    __device__ static const double* xpinv(const Inst& I) { return I.xpinv; }
+    __device__ static const double* Ky(const Inst& I) { return I.Ky; }
+};
+template <>
+struct Tabs<float> {
+    __device__ static const float* tab(const Inst& I) { return I.tab32; }
+    __device__ static const float* px(const Inst& I) { return I.px32; }
+    __device__ static const float* gL(const Inst& I) { return I.gL32; }
+    __device__ static const float* gR(const Inst& I) { return I.gR32; }
+    __device__ static const float* xpinv(const Inst& I) { return I.xpinv32; }
+    __device__ static const float* Ky(const Inst& I) { return I.Ky32; }
+};
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restrict__ insts, const Work* __restrict__ work, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -555,7 +783,12 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     const int i = w.i0 + lane;
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, ntab = I.ntab;
     const bool valid = i < N;
-    for (int r = wy; r < ntab; r += UPD_WARPS) stab[r * TILE + lane] = valid ? (C)I.tab[(size_t)r * ld + i] : (C)0;
+    const C* tabc = Tabs<C>::tab(I);
+    const C* pxc = Tabs<C>::px(I);
+    const C* gLc = Tabs<C>::gL(I);
+    const C* gRc = Tabs<C>::gR(I);
+    const C* Kyc = Tabs<C>::Ky(I);
+    for (int r = wy; r < ntab; r += UPD_WARPS) stab[r * TILE + lane] = valid ? tabc[(size_t)r * ld + i] : (C)0;
     __syncthreads();
     const S* src = static_cast<const S*>(I.f[stage - 1]);
     S* dst = static_cast<S*>(I.f[stage % 3]);
@@ -564,7 +797,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     const C cb = stage == 1 ? (C)1 : (stage == 2 ? (C)0.25 : (C)(2.0 / 3.0));
     const C dt = (C)I.dt;
     const C nwL = (C)I.misc[M_NWL], nwR = (C)I.misc[M_NWR];
-    const C xpi = valid ? (C)I.xpinv[i] : (C)0;
+    const C xpi = valid ? Tabs<C>::xpinv(I)[i] : (C)0;
     const C invtau = stab[(8 * Q + 4 * Tc) * TILE + lane];
     const bool force = I.accel_y != 0.0 && I.form != FORM_REDUCED1D;
     const int Tz = I.form == FORM_UNREDUCED ? I.Qz : 2;
@@ -573,7 +806,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     for (int k = w.k0 + wy; k < w.k1; k += UPD_WARPS) {
         const int kx = k / Tc, t = k - kx * Tc;
         const bool pos = kx < Q;
-        const C p = (C)I.px[kx];
+        const C p = pxc[kx];
         const S* row = src + (size_t)k * ld;
         // node values i-3 .. i+3 with ghost cells (Sec. III B): incoming populations take the
         // wall Maxwellian n_w g; outgoing ones the quadratic extrapolation of nodes 0..2.
@@ -586,14 +819,14 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
                 val = (C)row[j];
             } else if (j < 0) {
                 if (pos) {
-                    val = nwL * (C)I.gL[k];
+                    val = nwL * gLc[k];
                 } else {
                     const C f0 = (C)row[0], f1 = (C)row[1], f2 = (C)row[2];
                     val = j == -1 ? 3 * f0 - 3 * f1 + f2 : (j == -2 ? 6 * f0 - 8 * f1 + 3 * f2 : 10 * f0 - 15 * f1 + 6 * f2);
                 }
             } else {
                 if (!pos) {
-                    val = nwR * (C)I.gR[k];
+                    val = nwR * gRc[k];
                 } else {
                     const C f0 = (C)row[N - 1], f1 = (C)row[N - 2], f2 = (C)row[N - 3];
                     val = j == N ? 3 * f0 - 3 * f1 + f2 : (j == N + 1 ? 6 * f0 - 8 * f1 + 3 * f2 : 10 * f0 - 15 * f1 + 6 * f2);
@@ -603,20 +836,20 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
         }
         // right face (i + 1/2)
         C fr;
-        if (i + 1 == N) fr = pos ? (11 * v[3] - 7 * v[2] + 2 * v[1]) * sixth : nwR * (C)I.gR[k];
+        if (i + 1 == N) fr = pos ? (11 * v[3] - 7 * v[2] + 2 * v[1]) * sixth : nwR * gRc[k];
         else fr = pos ? weno_face(v[1], v[2], v[3], v[4], v[5]) : weno_face(v[6], v[5], v[4], v[3], v[2]);
         C fl = __shfl_up_sync(0xffffffffu, fr, 1);
         if (lane == 0) {
-            if (i == 0) fl = pos ? nwL * (C)I.gL[k] : (11 * v[3] - 7 * v[4] + 2 * v[5]) * sixth;
+            if (i == 0) fl = pos ? nwL * gLc[k] : (11 * v[3] - 7 * v[4] + 2 * v[5]) * sixth;
             else fl = pos ? weno_face(v[0], v[1], v[2], v[3], v[4]) : weno_face(v[5], v[4], v[3], v[2], v[1]);
         }
         if (!valid) continue;
         C L = -xpi * p * (fr - fl);
         if (force) {
             const int ky = t / Tz, kz = t - ky * Tz;
-            const double* Kr = I.Ky + ky * I.Qy;
+            const C* Kr = Kyc + ky * I.Qy;
             C d = 0;
-            for (int kp = 0; kp < I.Qy; ++kp) d += (C)Kr[kp] * (C)src[(size_t)(kx * Tc + kp * Tz + kz) * ld + i];
+            for (int kp = 0; kp < I.Qy; ++kp) d += Kr[kp] * (C)src[(size_t)(kx * Tc + kp * Tz + kz) * ld + i];
             L -= ay * d;
         }
         C tgt = 0;
@@ -672,8 +905,16 @@ static cudaError_t set_smem(size_t smem64, size_t smem32) {
     return e;
 }
 
-cudaError_t launch_nodal(const Inst* d_inst, int count, cudaStream_t s) {
-    k_nodal<<<count, 128, 0, s>>>(d_inst);
+cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int qmax, cudaStream_t s) {
+    static int done = 0;
+    const int wd = nodal_warp_doubles(qmax);
+    const size_t smem = (size_t)NOD_WARPS * wd * sizeof(double);
+    if (smem > 48 * 1024 && (int)smem > done) {
+        cudaError_t e = cudaFuncSetAttribute(k_nodal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        done = (int)smem;
+    }
+    k_nodal<<<n_nod, 32 * NOD_WARPS, smem, s>>>(d_inst, d_nod, wd);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ cudaError_t launch_resid(const Inst* d_inst, int count, int anchor_inst, double 
 cudaError_t launch_set_profiles(const Inst* d_inst, int inst, cudaStream_t s);
 
 // Per-node closure (chi, Pr, tau, gradients, projection tables, wall densities).
-cudaError_t launch_nodal(const Inst* d_inst, int count, cudaStream_t s);
+cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int qmax, cudaStream_t s);
 
 // RK stage `stage` (1..3) update of every ACTIVE instance.
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
