@@ -47,6 +47,10 @@ struct fdlb_ctx {
     size_t smem_upd_f64 = 0, smem_upd_f32 = 0;
     bool any_fp32 = false, any_fp64 = false;
     std::string err;
+    // CUDA graph of GRAPH_STEPS steps for one freeze tolerance (replayed by fdlb_step)
+    cudaGraphExec_t graph = nullptr;
+    double graph_tol = -1.0;
+    bool graph_failed = false;
     // optional per-kernel-class event timing (fdlb_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev[KK_COUNT];
@@ -54,6 +58,7 @@ struct fdlb_ctx {
     ~fdlb_ctx() {
         for (auto& v : ev)
             for (auto e : v) cudaEventDestroy(e);
+        if (graph) cudaGraphExecDestroy(graph);
     }
 };
 
@@ -310,7 +315,7 @@ int validate(const fdlb_params& p, std::string& why) {
 
 // Byte layout of one instance inside the workspace.
 struct Layout {
-    size_t tables = 0, fbuf = 0, node = 0, tab = 0, tab32 = 0, misc = 0, total = 0;
+    size_t tables = 0, fbuf = 0, node = 0, tab = 0, tab32 = 0, misc = 0, msum = 0, mcnt = 0, total = 0;
     int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0;
 };
 
@@ -329,7 +334,7 @@ Layout layout_of(const fdlb_params& p) {
     size_t nd = 0;
     // tables (doubles), each padded to 256 B
     auto add = [&](size_t n) { nd += al256(n * 8) / 8; };
-    add(2 * Q); add(MX); add(MX); add(Q); add(Q + 1); add(Q + 1); add(Q * Q);
+    add(2 * Q); add(MX); add(MX); add(MX8); add(MX8); add(Q); add(Q + 1); add(Q + 1); add(Q * Q);
     add(QYMAX); add(MYMAX); add(MYMAX); add(QYMAX * QYMAX);
     add(QZMAX); add(MYMAX); add(MYMAX); add(QZMAX * QZMAX);
     add(QYMAX * QYMAX);
@@ -347,7 +352,9 @@ Layout layout_of(const fdlb_params& p) {
     L.tab = al256((size_t)L.ntab * L.ld * 8);
     L.misc = al256(8 * 8);
     L.tab32 = p.precision == FDLB_FP32_STORAGE ? al256((size_t)L.ntab * L.ld * 4) : 0;
-    L.total = L.tables + 3 * L.fbuf + L.node + L.tab + L.tab32 + L.misc;
+    L.msum = al256((size_t)2 * p.qx_half * MOM_SUMS * L.ld * 8);
+    L.mcnt = al256((size_t)(L.ld / TILE) * 4);
+    L.total = L.tables + 3 * L.fbuf + L.node + L.tab + L.tab32 + L.misc + L.msum + L.mcnt;
     return L;
 }
 
@@ -363,9 +370,9 @@ void count_work(const std::vector<fdlb_params>& p, int& n_mom, int& n_upd, int& 
     for (auto& q : p) {
         Layout L = layout_of(q);
         int tiles = (q.nx + TILE - 1) / TILE;
-        n_mom += tiles;
+        n_mom += tiles * 2 * q.qx_half;
         n_upd += tiles * ((L.K + KC - 1) / KC);
-        n_nod += (q.nx + NOD_WARPS - 1) / NOD_WARPS;
+        n_nod += tiles * 3;
     }
 }
 
@@ -422,6 +429,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     c->d_resid_all = reinterpret_cast<double*>(take(sizeof(double) * count));
 
     std::vector<Work> wm, wu, wn;
+    std::vector<std::pair<int*, size_t>> counters;
     std::vector<char> staging;        // host image of all table regions
     std::vector<std::pair<size_t, size_t>> regions;   // (offset, size) of table regions
     size_t max_smem64 = 0, max_smem32 = 0;
@@ -471,6 +479,9 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             for (int k = 0; k < Q; ++k) { h[k] = xr.x[k]; h[Q + k] = -xr.x[k]; }
             h = put(&I.xq, MX); for (int m = 0; m < MX; ++m) h[m] = xa.x[m];
             h = put(&I.xw, MX); for (int m = 0; m < MX; ++m) h[m] = xa.w[m];
+            Rule xa8 = make_rule(0, MX8);
+            h = put(&I.xq8, MX8); for (int m = 0; m < MX8; ++m) h[m] = xa8.x[m];
+            h = put(&I.xw8, MX8); for (int m = 0; m < MX8; ++m) h[m] = xa8.w[m];
             h = put(&I.xa, Q); for (int l = 0; l < Q; ++l) h[l] = xr.alpha[l];
             double* hb = put(&I.xb, Q + 1);
             double* hib = put(&I.xib, Q + 1);
@@ -619,16 +630,19 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         I.tab = reinterpret_cast<double*>(take(L.tab));
         I.tab32 = L.tab32 ? reinterpret_cast<float*>(take(L.tab32)) : nullptr;
         I.misc = reinterpret_cast<double*>(take(L.misc));
+        I.msum = reinterpret_cast<double*>(take(L.msum));
+        I.mcnt = reinterpret_cast<int*>(take(L.mcnt));
+        counters.push_back({I.mcnt, L.mcnt});
         I.status = c->d_status_all + ii;
         I.steps = c->d_steps_all + ii;
         c->inst.push_back(I);
 
         int tiles = (N + TILE - 1) / TILE;
         for (int t = 0; t < tiles; ++t) {
-            wm.push_back({ii, t * TILE, 0, L.K});
+            for (int kx = 0; kx < 2 * Q; ++kx) wm.push_back({ii, t * TILE, kx, t});
             for (int k0 = 0; k0 < L.K; k0 += KC) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + KC)});
+            for (int role = 0; role < 3; ++role) wn.push_back({ii, t * TILE, role, 0});
         }
-        for (int i0 = 0; i0 < N; i0 += NOD_WARPS) wn.push_back({ii, i0, 0, 0});
         c->qmax = std::max(c->qmax, Q);
         size_t sm = (size_t)L.ntab * TILE;
         if (p.precision == FDLB_FP64) max_smem64 = std::max(max_smem64, sm * 8), c->any_fp64 = true;
@@ -651,6 +665,9 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_mom, wm.data(), sizeof(Work) * n_mom, cudaMemcpyHostToDevice, s), "upload work");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_upd, wu.data(), sizeof(Work) * n_upd, cudaMemcpyHostToDevice, s), "upload work");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_nod, wn.data(), sizeof(Work) * n_nod, cudaMemcpyHostToDevice, s), "upload work");
+    for (auto& cn : counters)
+        if (!rc) rc = cuda_check(c, cudaMemsetAsync(cn.first, 0, cn.second, s), "clear counters");
+    if (!rc) rc = cuda_check(c, prepare_kernels(c->smem_upd_f64, c->smem_upd_f32, c->qmax), "kernel attributes");
     if (!rc) rc = cuda_check(c, launch_setup(c->d_inst, count, s), "setup kernel");
     if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, n_mom, 0, c->any_fp64, c->any_fp32, s), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, count, 1, 0.0, c->d_resid_all, s), "residual kernel");
@@ -671,9 +688,51 @@ extern "C" int fdlb_info(const fdlb_ctx* ctx, int32_t inst, int32_t* nx, int32_t
     return FDLB_OK;
 }
 
+static const int GRAPH_STEPS = 16;
+
+// Capture GRAPH_STEPS steps into an executable graph (kernels only; no host synchronisation
+// inside).  The legacy default stream cannot be captured: then steps are launched directly.
+static bool ensure_graph(fdlb_ctx* c, double tol) {
+    if (c->graph && c->graph_tol == tol) return true;
+    if (c->graph_failed || c->stream == nullptr) return false;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        c->graph_failed = true;
+        cudaGetLastError();
+        return false;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < GRAPH_STEPS && e == cudaSuccess; ++s) e = step_once(c, tol);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        c->graph_failed = true;
+        cudaGetLastError();
+        return false;
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        c->graph_failed = true;
+        cudaGetLastError();
+        return false;
+    }
+    c->graph_tol = tol;
+    return true;
+}
+
 extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
     if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_step: null context");
     if (nsteps < 0 || !(freeze_tol >= 0)) return fail(c, FDLB_EINVAL, "fdlb_step: nsteps >= 0 and freeze_tol >= 0 required");
+    if (!c->prof && nsteps >= GRAPH_STEPS && ensure_graph(c, freeze_tol)) {
+        while (nsteps >= GRAPH_STEPS) {
+            cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+            if (e != cudaSuccess) return cuda_check(c, e, "fdlb_step graph launch");
+            nsteps -= GRAPH_STEPS;
+        }
+    }
     for (int64_t s = 0; s < nsteps; ++s) {
         cudaError_t e = step_once(c, freeze_tol);
         if (e != cudaSuccess) return cuda_check(c, e, "fdlb_step launch");

@@ -11,10 +11,12 @@ constexpr int QYMAX = 8;        // full-range order on y
 constexpr int QZMAX = 8;        // full-range order on z
 constexpr int TCMAX = QYMAX * QZMAX;
 constexpr int MX = 16;          // auxiliary half-range rule used for the x projections
+constexpr int MX8 = 8;          // shorter auxiliary rule when |u_x|/sqrt(T) is small (see k_nodal)
 constexpr int MYMAX = 8;        // auxiliary full-range rule (exact: 2M > Q + 2)
 constexpr int NTERMS = 13;      // monomials of f^S + tau J1
 constexpr int TILE = 32;        // nodes per tile (one warp lane per node)
-constexpr int NOD_WARPS = 4;    // nodes per k_nodal block (one warp per node)
+constexpr int NOD_WARPS = 8;    // warps per k_nodal block (a block serves one 32-node tile)
+constexpr int MOM_SUMS = 14;    // raw moment sums per node
 
 enum Form : int { FORM_UNREDUCED = 0, FORM_REDUCED2D = 1, FORM_REDUCED1D = 2 };
 
@@ -22,6 +24,7 @@ enum Form : int { FORM_UNREDUCED = 0, FORM_REDUCED2D = 1, FORM_REDUCED1D = 2 };
 enum NodeRow : int {
     R_N = 0, R_UX, R_UY, R_T, R_QX, R_QY, R_PXX, R_PXY, R_SNEG, R_SPOS,
     R_PREV_N, R_PREV_UX, R_PREV_UY, R_PREV_T,
+    R_LNN, R_LNT, R_LNCHI,     // ln n, ln T, ln chi(eta0 n) of the current moments
     NROWS
 };
 
@@ -43,6 +46,8 @@ struct Inst {
     const double* px;          // [2Q]: +p_1..+p_Q, -p_1..-p_Q
     const double* xq;          // [Mx] aux half-range nodes
     const double* xw;          // [Mx] aux half-range weights
+    const double* xq8;         // [MX8] 8-point aux half-range nodes
+    const double* xw8;         // [MX8] 8-point aux half-range weights
     const double* xa;          // [Q]   recurrence alpha_l
     const double* xb;          // [Q+1] recurrence b_l = sqrt(beta_l), b_0 = 0
     const double* xib;         // [Q+1] 1/b_l (l >= 1)
@@ -80,6 +85,8 @@ struct Inst {
     double* node;              // [NROWS*ld]
     double* tab;               // [ntab*ld] projection table (see below)
     double* misc;              // [NMISC]
+    double* msum;              // [2Q][14][ld] per-x-velocity partial raw moment sums
+    int* mcnt;                 // [tiles] arrival tickets of the moment CTAs of a tile (zero between uses)
     int* status;
     long long* steps;
 };

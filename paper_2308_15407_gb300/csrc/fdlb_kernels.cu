@@ -27,6 +27,8 @@
 
 namespace fdlb {
 
+__constant__ double c_inv[13] = {0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12};
+
 __constant__ int c_mono[NTERMS][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0},
                                       {3, 0, 0}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 3, 0}, {0, 1, 2}};
 
@@ -261,8 +263,6 @@ __global__ void k_profiles(Inst* insts, int inst) {
 // ---------------------------------------------------------------------------
 // moments
 // ---------------------------------------------------------------------------
-constexpr int MOM_WARPS = 8;
-constexpr int NSUM = 14;
 constexpr int NTW = 6;     // transverse weights: mt, mt py, mt py^2, mt py^3, et, et py
 
 // Inner (transverse) running sum of w(t) f over t.  FP64 storage: an FP64 FMA.  FP32
@@ -295,67 +295,80 @@ struct InnerSum<float> {
 };
 
 // Per node: the 14 raw sums over all velocities, factorised as sum_kx px^a (sum_t w_j(t) f).
+// One block per (instance, 32-node tile, x-velocity kx); its 4 warps split the transverse index.
+// Each block writes its 14 partial sums for kx; the last block of a tile to arrive (ticket from
+// an atomic counter) adds the 2Q partials in kx order -- so the result does not depend on the
+// arrival order -- converts them to n, u, T, q, Pi and resets the ticket.
+constexpr int MOM3_WARPS = 4;
+
 template <typename S>
-__global__ void __launch_bounds__(TILE * MOM_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
-    __shared__ double red[NSUM][MOM_WARPS][TILE];
-    __shared__ double sw[NTW][TCMAX];
-    __shared__ float swh[NTW][TCMAX], swl[NTW][TCMAX];
+__global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
+    __shared__ double part[MOM3_WARPS][NTW][TILE];
+    __shared__ int last;
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE) return;
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
-    const int lane = threadIdx.x, g = threadIdx.y;
-    const int i = w.i0 + lane;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = w.i0 + lane, kx = w.k0, tile = w.k1;
     const int ld = I.ld, Tc = I.Tc, Q = I.Q;
     const bool valid = i < I.N;
-    for (int o = g * TILE + lane; o < NTW * Tc; o += TILE * MOM_WARPS) {
-        const int j = o / Tc, t = o - j * Tc;
-        sw[j][t] = I.tw[o];
-        swh[j][t] = I.twh[o];
-        swl[j][t] = I.twl[o];
+    const S* f = static_cast<const S*>(I.f[buf]) + (size_t)kx * Tc * ld + (valid ? i : 0);
+    InnerSum<S> a[NTW];
+    for (int t = g; t < Tc; t += MOM3_WARPS) {
+        const S fv = valid ? f[(size_t)t * ld] : (S)0;
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], I.twh[j * Tc + t], I.twl[j * Tc + t]);
     }
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) part[g][j][lane] = a[j].value();
     __syncthreads();
-    const S* f = static_cast<const S*>(I.f[buf]);
-    double acc[NSUM];
+    if (g == 0) {
+        double S6[NTW];
 #pragma unroll
-    for (int j = 0; j < NSUM; ++j) acc[j] = 0.0;
-    for (int kx = g; kx < 2 * Q; kx += MOM_WARPS) {
-        InnerSum<S> a[NTW];
-        const S* row = f + (size_t)kx * Tc * ld + (valid ? i : 0);
-        for (int t = 0; t < Tc; ++t) {
-            const S fv = valid ? row[(size_t)t * ld] : (S)0;
-#pragma unroll
-            for (int j = 0; j < NTW; ++j) a[j].add(fv, sw[j][t], swh[j][t], swl[j][t]);
+        for (int j = 0; j < NTW; ++j) {
+            double v = 0.0;
+            for (int q = 0; q < MOM3_WARPS; ++q) v += part[q][j][lane];
+            S6[j] = v;
         }
-        const double S0 = a[0].value(), S1 = a[1].value(), S2 = a[2].value(), S3 = a[3].value();
-        const double S4 = a[4].value(), S5 = a[5].value();
         const double p = I.px[kx], p2 = p * p, p3 = p2 * p;
-        acc[0] += S0;
-        if (kx >= Q) acc[1] = fma(p, S0, acc[1]); else acc[2] = fma(p, S0, acc[2]);
-        acc[3] += S1;
-        acc[4] = fma(p2, S0, acc[4]);
-        acc[5] = fma(p, S1, acc[5]);
-        acc[6] += S2;
-        acc[7] += S4;
-        acc[8] = fma(p3, S0, acc[8]);
-        acc[9] = fma(p, S2, acc[9]);
-        acc[10] = fma(p2, S1, acc[10]);
-        acc[11] += S3;
-        acc[12] = fma(p, S4, acc[12]);
-        acc[13] += S5;
-    }
+        // 0 n, 1 sneg, 2 spos, 3 sy, 4 sxx, 5 sxy, 6 syy, 7 se, 8 sxxx, 9 sxyy, 10 sxxy, 11 syyy, 12 sxe, 13 sye
+        double o[MOM_SUMS];
+        o[0] = S6[0];
+        o[1] = kx >= Q ? p * S6[0] : 0.0;
+        o[2] = kx >= Q ? 0.0 : p * S6[0];
+        o[3] = S6[1];
+        o[4] = p2 * S6[0];
+        o[5] = p * S6[1];
+        o[6] = S6[2];
+        o[7] = S6[4];
+        o[8] = p3 * S6[0];
+        o[9] = p * S6[2];
+        o[10] = p2 * S6[1];
+        o[11] = S6[3];
+        o[12] = p * S6[4];
+        o[13] = S6[5];
+        double* dst = I.msum + (size_t)kx * MOM_SUMS * ld + i;
+        if (valid)
 #pragma unroll
-    for (int j = 0; j < NSUM; ++j) red[j][g][lane] = acc[j];
+            for (int j = 0; j < MOM_SUMS; ++j) dst[(size_t)j * ld] = o[j];
+        __threadfence();
+    }
     __syncthreads();
-    if (g != 0 || !valid) return;
-    double s[NSUM];
+    if (threadIdx.x == 0) last = atomicAdd(I.mcnt + tile, 1) == 2 * Q - 1;
+    __syncthreads();
+    if (!last || g != 0) return;
+    __threadfence();
+    if (threadIdx.x == 0) I.mcnt[tile] = 0;
+    if (!valid) return;
+    double s[MOM_SUMS];
 #pragma unroll
-    for (int j = 0; j < NSUM; ++j) {
-        double v = 0.0;
-        for (int q = 0; q < MOM_WARPS; ++q) v += red[j][q][lane];
-        s[j] = v;
+    for (int j = 0; j < MOM_SUMS; ++j) s[j] = 0.0;
+    for (int q = 0; q < 2 * Q; ++q) {
+        const double* src = I.msum + (size_t)q * MOM_SUMS * ld + i;
+#pragma unroll
+        for (int j = 0; j < MOM_SUMS; ++j) s[j] += __ldcg(src + (size_t)j * ld);
     }
-    // s: 0 n, 1 sneg, 2 spos, 3 sy, 4 sxx, 5 sxy, 6 syy, 7 se, 8 sxxx, 9 sxyy, 10 sxxy, 11 syyy, 12 sxe, 13 sye
     const double n = s[0], sx = s[1] + s[2];
     const double ux = sx / n, uy = s[3] / n;
     const double Pxx = s[4] - n * ux * ux, Pxy = s[5] - n * ux * uy, Pyy = s[6] - n * uy * uy;
@@ -378,229 +391,267 @@ __global__ void __launch_bounds__(TILE * MOM_WARPS) k_moments(const Inst* __rest
     nd[R_PXY * ld + i] = Pxy;
     nd[R_SNEG * ld + i] = s[1];
     nd[R_SPOS * ld + i] = s[2];
+    nd[R_LNN * ld + i] = log(n);
+    nd[R_LNT * ld + i] = log(T);
+    nd[R_LNCHI * ld + i] = log(chi_cs(I.eta0 * n));
 }
 
 // ---------------------------------------------------------------------------
-// per-node closure and projection tables: one warp per node
+// per-node closure and projection tables
 // ---------------------------------------------------------------------------
-// Shared doubles per warp: scalars (32) | partial products | G (8Q) | Py (4 QYMAX) | Pz (3 QZMAX).
-__host__ __device__ inline int nodal_partials(int Q) { return 128 * Q > 448 ? 128 * Q : 448; }
-__host__ __device__ inline int nodal_warp_doubles(int Q) { return 32 + nodal_partials(Q) + 8 * Q + 4 * QYMAX + 3 * QZMAX; }
+// Three independent block roles per 32-node tile (lane = node, so every FP64 instruction runs
+// with full lanes): role 0 / 1 = half-range x projection of the positive / negative half-axis,
+// role 2 = gradients, closure, coefficients, y and z projections and the transverse factors.
+// Shared doubles: role 0/1: [NOD_WARPS][4Q][32] partials + [4Q][32] sums;
+//                 role 2:   [20][32] scalars + Py [4 QYMAX][32] + Pz [3 QZMAX][32] + A [8 QYMAX][32].
+__host__ __device__ inline int nodal_smem_doubles(int qmax) {
+    const int r01 = (NOD_WARPS + 1) * 4 * qmax * TILE;
+    const int r2 = (20 + 4 * QYMAX + 3 * QZMAX + 8 * QYMAX) * TILE;
+    return r01 > r2 ? r01 : r2;
+}
 
-__global__ void __launch_bounds__(32 * NOD_WARPS) k_nodal(const Inst* __restrict__ insts, const Work* __restrict__ work, int wdoubles) {
+template <int QB>
+__global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restrict__ insts, const Work* __restrict__ work) {
     extern __shared__ __align__(16) double nsm[];
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int i = w.i0 + wid;
+    const int role = w.k0;
+    const int i = w.i0 + lane;
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc;
-    if (i >= N) return;                 // whole warp; only warp-level synchronisation below
-    double* sc = nsm + wid * wdoubles;
-    double* Gp = sc + 32;
-    double* Gs = Gp + nodal_partials(Q);
-    double* Py = Gs + 8 * Q;
-    double* Pz = Py + 4 * QYMAX;
+    const bool valid = i < N;
+    const int ic = valid ? i : N - 1;           // padding lanes work on a real node, write nothing
     const double* nd = I.node;
-    if (i == 0 && lane == 0) {
-        // zero net mass flux through each wall (Sec. III B): the outgoing wall-face flux is the
-        // quadratic reconstruction (11 f_1 - 7 f_2 + 2 f_3)/6 of the outgoing populations.
-        const double oL = (11.0 * nd[R_SNEG * ld + 0] - 7.0 * nd[R_SNEG * ld + 1] + 2.0 * nd[R_SNEG * ld + 2]) / 6.0;
-        const double oR = (11.0 * nd[R_SPOS * ld + N - 1] - 7.0 * nd[R_SPOS * ld + N - 2] + 2.0 * nd[R_SPOS * ld + N - 3]) / 6.0;
-        I.misc[M_NWL] = -oL / I.misc[M_INL];
-        I.misc[M_NWR] = -oR / I.misc[M_INR];
-    }
-    // ---- gradients (Sec. III B 3): lane j < 7 takes stencil point j
-    double gn = 0.0, gc = 0.0, gT = 0.0, gux = 0.0, guy = 0.0;
-    if (lane < 7) {
-        int idx;
-        double wj;
-        if (i < 3) { idx = lane; wj = I.gst[i * 7 + lane]; }
-        else if (i > N - 4) { const int m = N - 1 - i; idx = N - 1 - lane; wj = -I.gst[m * 7 + lane]; }
-        else {
-            const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
-            idx = i - 3 + lane;
-            wj = cen[lane];
-        }
-        if (wj != 0.0) {
-            const double nj = nd[R_N * ld + idx], Tj = nd[R_T * ld + idx];
-            gn = wj * log(nj);
-            gc = wj * log(chi_cs(I.eta0 * nj));
-            gT = wj * log(Tj);
-            gux = wj * nd[R_UX * ld + idx];
-            guy = wj * nd[R_UY * ld + idx];
-        }
-    }
+    if (role < 2) {
+        // ---- half-range x projection (Sec. III A 2), half-axis `role`.  With |v| < 0.02 and
+        // Q <= 12 the 8-point auxiliary rule is used (exact for v = 0 up to degree 15 >= Q + 2;
+        // the neglected part of exp(q v) is below 1e-14 relative) with exp(q v - v^2/2) from its
+        // Taylor series (|argument| < 0.12, 12 terms).  Warp w takes auxiliary points w, w + 8.
+        const double T = nd[R_T * ld + ic], ux = nd[R_UX * ld + ic];
+        const double sT = sqrt(T), uu = role ? -ux : ux, v = uu / sT;
+        // one rule per block so that the warps agree: the largest |v| of the tile decides
+        double av = valid ? fabs(v) : 0.0;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        gn += __shfl_xor_sync(0xffffffffu, gn, o);
-        gc += __shfl_xor_sync(0xffffffffu, gc, o);
-        gT += __shfl_xor_sync(0xffffffffu, gT, o);
-        gux += __shfl_xor_sync(0xffffffffu, gux, o);
-        guy += __shfl_xor_sync(0xffffffffu, guy, o);
+        for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
+        __shared__ int use_short;
+        if (threadIdx.x == 0) use_short = 0;
+        __syncthreads();
+        if (lane == 0) atomicOr(&use_short, av < 0.02 ? 1 : 2);
+        __syncthreads();
+        const bool short_rule = use_short == 1 && Q <= 12;
+        const int M = short_rule ? MX8 : MX;
+        double G[4][QB];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int l = 0; l < QB; ++l) G[a][l] = 0.0;
+        for (int m = wid; m < M; m += NOD_WARPS) {
+            const double q = short_rule ? I.xq8[m] : I.xq[m];
+            const double Wm = short_rule ? I.xw8[m] : I.xw[m];
+            const double z = fma(q, v, -0.5 * v * v);
+            double ez;
+            if (short_rule) {
+                ez = 1.0;
+#pragma unroll
+                for (int j = 12; j >= 1; --j) ez = fma(ez * z, c_inv[j], 1.0);
+            } else {
+                ez = exp(z);
+            }
+            const double x = sT * q, E = Wm * ez;
+            const double y = x - uu, e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+            double hm = 0.0, h = I.x_h0;
+#pragma unroll
+            for (int l = 0; l < QB; ++l) {
+                if (l < Q) {
+                    G[0][l] = fma(E, h, G[0][l]);
+                    G[1][l] = fma(e1, h, G[1][l]);
+                    G[2][l] = fma(e2, h, G[2][l]);
+                    G[3][l] = fma(e3, h, G[3][l]);
+                    const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
+                    hm = h;
+                    h = hn;
+                }
+            }
+        }
+        double* part = nsm;                                  // [NOD_WARPS][4Q][32]
+        double* sum = nsm + NOD_WARPS * 4 * Q * TILE;        // [4Q][32]
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int l = 0; l < QB; ++l)
+                if (l < Q) part[((wid * 4 + a) * Q + l) * TILE + lane] = G[a][l];
+        __syncthreads();
+        for (int r = wid; r < 4 * Q; r += NOD_WARPS) {
+            double s = 0.0;
+            for (int q = 0; q < NOD_WARPS; ++q) s += part[(q * 4 * Q + r) * TILE + lane];
+            sum[r * TILE + lane] = s;
+        }
+        __syncthreads();
+        for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
+            const int a = o / Q, k = o - a * Q;
+            double s = 0.0;
+            for (int l = 0; l < Q; ++l) s = fma(I.xH[l * Q + k], sum[(a * Q + l) * TILE + lane], s);
+            if (role && (a & 1)) s = -s;
+            if (valid) {
+                const size_t r = (size_t)(a * 2 * Q + role * Q + k) * ld + i;
+                I.tab[r] = s;
+                if (I.tab32) I.tab32[r] = (float)s;
+            }
+        }
+        return;
     }
-    // ---- closure and the 13 coefficients (lane 0)
-    if (lane == 0) {
+    // ---------------- role 2
+    double* sc = nsm;                                              // [20][32]
+    double* Py = sc + 20 * TILE;                                   // [4 QYMAX][32]
+    double* Pz = Py + 4 * QYMAX * TILE;                            // [3 QZMAX][32]
+    double* Ay = Pz + 3 * QZMAX * TILE;                            // [8 QYMAX][32]
+    const double T = nd[R_T * ld + ic], sT = sqrt(T);
+    const int Qy = I.Qy, Qz = I.Qz;
+    if (wid == NOD_WARPS - 1) {
+        if (w.i0 == 0 && lane == 0) {
+            // zero net mass flux through each wall (Sec. III B): the outgoing wall-face flux is
+            // the quadratic reconstruction (11 f_1 - 7 f_2 + 2 f_3)/6 of outgoing populations.
+            const double oL = (11.0 * nd[R_SNEG * ld + 0] - 7.0 * nd[R_SNEG * ld + 1] + 2.0 * nd[R_SNEG * ld + 2]) / 6.0;
+            const double oR = (11.0 * nd[R_SPOS * ld + N - 1] - 7.0 * nd[R_SPOS * ld + N - 2] + 2.0 * nd[R_SPOS * ld + N - 3]) / 6.0;
+            I.misc[M_NWL] = -oL / I.misc[M_INL];
+            I.misc[M_NWR] = -oR / I.misc[M_INR];
+        }
+        // ---- gradients (Sec. III B 3), closure (Eqs. chi, prandtl, viscosity, tau) and the
+        // 13 coefficients of f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j) (Eq. j1)
+        const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
+        double gn = 0.0, gc = 0.0, gT = 0.0, gux = 0.0, guy = 0.0;
+        for (int j = 0; j < 7; ++j) {
+            int idx;
+            double wj;
+            if (ic < 3) { idx = j; wj = I.gst[ic * 7 + j]; }
+            else if (ic > N - 4) { const int m = N - 1 - ic; idx = N - 1 - j; wj = -I.gst[m * 7 + j]; }
+            else { idx = ic - 3 + j; wj = cen[j]; }
+            gn = fma(wj, nd[R_LNN * ld + idx], gn);
+            gc = fma(wj, nd[R_LNCHI * ld + idx], gc);
+            gT = fma(wj, nd[R_LNT * ld + idx], gT);
+            gux = fma(wj, nd[R_UX * ld + idx], gux);
+            guy = fma(wj, nd[R_UY * ld + idx], guy);
+        }
         const double k_mu = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
         const double k_pd = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * CUDART_PI));
-        const double xi = I.xpinv[i];
+        const double xi = I.xpinv[ic];
         const double Gr = (2.0 * gn + gc + gT) * xi, Br = gT * xi, Ur = gux * xi, Vr = guy * xi;
-        const double n = nd[R_N * ld + i], ux = nd[R_UX * ld + i], uy = nd[R_UY * ld + i], T = nd[R_T * ld + i];
-        const double qx = nd[R_QX * ld + i], qy = nd[R_QY * ld + i];
+        const double n = nd[R_N * ld + ic];
+        const double qx = nd[R_QX * ld + ic], qy = nd[R_QY * ld + ic];
         const double eta = I.eta0 * n, chi = chi_cs(eta), br = 4.0 * eta, brc = br * chi;
         const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_mu * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
-        const double mu = I.mu0c * sqrt(T) * (1.0 / chi + 0.8 * br + k_mu * br * br * chi);
-        const double tau = mu / (n * T);
-        // f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j)  (Sec. II A, Eq. j1)
-        const double A = (1.0 - Pr) / (5.0 * n * T * T), W = -tau * brc, iT = 1.0 / T;
-        sc[0] = 1.0 - W * Ur;
-        sc[1] = -5.0 * A * qx + W * (Gr - 1.5 * Br);
-        sc[2] = -5.0 * A * qy;
-        sc[3] = W * 0.6 * Ur * iT;
-        sc[4] = W * 0.2 * Ur * iT;
-        sc[5] = sc[4];
-        sc[6] = I.j1_shear ? W * 0.4 * Vr * iT : 0.0;
-        sc[7] = A * qx * iT + W * 0.3 * Br * iT;
-        sc[8] = sc[7];
-        sc[9] = sc[7];
-        sc[10] = A * qy * iT;
-        sc[11] = sc[10];
-        sc[12] = sc[10];
-        sc[13] = T;
-        sc[14] = ux;
-        sc[15] = uy;
-        sc[16] = n;
-        sc[17] = 1.0 / tau;
-    }
-    __syncwarp();
-    // ---- half-range x projection (Sec. III A 2): lane = half * 16 + aux point
-    {
-        const int half = lane >> 4, m = lane & 15;
-        const double T = sc[13], uu = half ? -sc[14] : sc[14];
-        const double sT = sqrt(T), v = uu / sT;
-        const double q = I.xq[m], x = sT * q;
-        const double E = I.xw[m] * exp(fma(q, v, -0.5 * v * v));
-        const double y = x - uu, e1 = E * y, e2 = e1 * y, e3 = e2 * y;
-        double hm = 0.0, h = I.x_h0;
-        for (int l = 0; l < Q; ++l) {
-            Gp[(0 * Q + l) * 32 + lane] = E * h;
-            Gp[(1 * Q + l) * 32 + lane] = e1 * h;
-            Gp[(2 * Q + l) * 32 + lane] = e2 * h;
-            Gp[(3 * Q + l) * 32 + lane] = e3 * h;
-            const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
-            hm = h;
-            h = hn;
-        }
-    }
-    __syncwarp();
-    for (int o = lane; o < 8 * Q; o += 32) {
-        const int hf = o / (4 * Q), r = o - hf * 4 * Q;            // r = a Q + l
-        const double* src = Gp + r * 32 + hf * 16;
-        double s = 0.0;
+        const double iT = 1.0 / T;
+        const double mu = I.mu0c * sT * (1.0 / chi + 0.8 * br + k_mu * br * br * chi);
+        const double tau = mu * iT / n;
+        const double A = (1.0 - Pr) * 0.2 * iT * iT / n, W = -tau * brc;
+        sc[0 * TILE + lane] = 1.0 - W * Ur;
+        sc[1 * TILE + lane] = -5.0 * A * qx + W * (Gr - 1.5 * Br);
+        sc[2 * TILE + lane] = -5.0 * A * qy;
+        sc[3 * TILE + lane] = W * 0.6 * Ur * iT;
+        sc[4 * TILE + lane] = W * 0.2 * Ur * iT;
+        sc[5 * TILE + lane] = W * 0.2 * Ur * iT;
+        sc[6 * TILE + lane] = I.j1_shear ? W * 0.4 * Vr * iT : 0.0;
+        const double c3 = A * qx * iT + W * 0.3 * Br * iT, cy = A * qy * iT;
+        sc[7 * TILE + lane] = c3;
+        sc[8 * TILE + lane] = c3;
+        sc[9 * TILE + lane] = c3;
+        sc[10 * TILE + lane] = cy;
+        sc[11 * TILE + lane] = cy;
+        sc[12 * TILE + lane] = cy;
+        sc[13 * TILE + lane] = n;
+        sc[14 * TILE + lane] = 1.0 / tau;
+    } else if (I.form != FORM_REDUCED1D && (wid < 4 || I.form == FORM_UNREDUCED)) {
+        // ---- full-range projections (App. A): warps 0..3 row a = wid of Py (p_y - u_y)^a g,
+        // warps 4..6 row a = wid - 4 of Pz (p_z^a g); sum over the auxiliary rule in registers.
+        const bool ydir = wid < 4;
+        const int a = ydir ? wid : wid - 4;
+        const int Qn = ydir ? Qy : Qz, M = ydir ? I.My : I.Mz;
+        const double* aq = ydir ? I.yq : I.zq;
+        const double* aw = ydir ? I.yw : I.zw;
+        const double* H = ydir ? I.yH : I.zH;
+        const double u0 = ydir ? nd[R_UY * ld + ic] : 0.0;
+        double G[QYMAX > QZMAX ? QYMAX : QZMAX];
 #pragma unroll
-        for (int m = 0; m < 16; ++m) s += src[m];
-        Gs[o] = s;
+        for (int l = 0; l < QYMAX; ++l) G[l] = 0.0;
+        for (int m = 0; m < M; ++m) {
+            const double y = sT * aq[m], x = u0 + y;
+            double e = aw[m];
+            for (int j = 0; j < a; ++j) e *= y;
+            double hm = 0.0, h = 1.0;
+#pragma unroll
+            for (int l = 0; l < QYMAX; ++l) {
+                if (l < Qn) {
+                    G[l] = fma(e, h, G[l]);
+                    const double hn = (x * h - I.fsq[l] * hm) * I.fisq[l + 1];
+                    hm = h;
+                    h = hn;
+                }
+            }
+        }
+        double* P = ydir ? Py + a * QYMAX * TILE : Pz + a * QZMAX * TILE;
+        for (int k2 = 0; k2 < Qn; ++k2) {
+            double s = 0.0;
+#pragma unroll
+            for (int l = 0; l < QYMAX; ++l)
+                if (l < Qn) s = fma(H[l * Qn + k2], G[l], s);
+            P[k2 * TILE + lane] = s;
+        }
     }
-    __syncwarp();
-    for (int o = lane; o < 8 * Q; o += 32) {
-        const int a = o / (2 * Q), kx = o - a * 2 * Q, hf = kx >= Q ? 1 : 0, k = kx - hf * Q;
-        const double* gg = Gs + hf * 4 * Q + a * Q;
-        double s = 0.0;
-        for (int l = 0; l < Q; ++l) s = fma(I.xH[l * Q + k], gg[l], s);
-        if (hf && (a & 1)) s = -s;
-        const size_t r = (size_t)(a * 2 * Q + kx) * ld + i;
-        I.tab[r] = s;
-        if (I.tab32) I.tab32[r] = (float)s;
-    }
-    // ---- full-range y and z projections (App. A)
+    __syncthreads();
     if (I.form != FORM_REDUCED1D) {
-        __syncwarp();
-        const double T = sc[13], sT = sqrt(T);
-        const int Qy = I.Qy, Qz = I.Qz;
-        if (lane < I.My) {
-            const double y = sT * I.yq[lane], x = sc[15] + y, E = I.yw[lane];
-            const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
-            double hm = 0.0, h = 1.0;
-            for (int l = 0; l < Qy; ++l) {
-                Gp[(0 * QYMAX + l) * 8 + lane] = E * h;
-                Gp[(1 * QYMAX + l) * 8 + lane] = e1 * h;
-                Gp[(2 * QYMAX + l) * 8 + lane] = e2 * h;
-                Gp[(3 * QYMAX + l) * 8 + lane] = e3 * h;
-                const double hn = (x * h - I.fsq[l] * hm) * I.fisq[l + 1];
-                hm = h;
-                h = hn;
-            }
-        }
-        if (I.form == FORM_UNREDUCED && lane >= 16 && lane < 16 + I.Mz) {
-            const int m = lane - 16;
-            const double y = sT * I.zq[m], E = I.zw[m];
-            const double e1 = E * y, e2 = e1 * y;
-            double hm = 0.0, h = 1.0;
-            for (int l = 0; l < Qz; ++l) {
-                Gp[256 + (0 * QZMAX + l) * 8 + m] = E * h;
-                Gp[256 + (1 * QZMAX + l) * 8 + m] = e1 * h;
-                Gp[256 + (2 * QZMAX + l) * 8 + m] = e2 * h;
-                const double hn = (y * h - I.fsq[l] * hm) * I.fisq[l + 1];
-                hm = h;
-                h = hn;
-            }
-        }
-        __syncwarp();
-        for (int o = lane; o < 4 * Qy; o += 32) {
-            const int a = o / Qy, k = o - a * Qy;
+        // A[a][c'][ky] = n sum over monomials (a, b, c = 2 c') of coef * Py[b][ky]
+        for (int o = wid; o < 8 * Qy; o += NOD_WARPS) {
+            const int ac = o / Qy, ky = o - ac * Qy, a = ac >> 1, c2 = ac & 1;
             double s = 0.0;
-            for (int l = 0; l < Qy; ++l) {
-                double t = 0.0;
-                for (int m = 0; m < I.My; ++m) t += Gp[(a * QYMAX + l) * 8 + m];
-                s = fma(I.yH[l * Qy + k], t, s);
-            }
-            Py[a * QYMAX + k] = s;
+            for (int j = 0; j < NTERMS; ++j)
+                if (c_mono[j][0] == a && c_mono[j][2] == 2 * c2) s = fma(sc[j * TILE + lane], Py[(c_mono[j][1] * QYMAX + ky) * TILE + lane], s);
+            Ay[o * TILE + lane] = sc[13 * TILE + lane] * s;
         }
-        if (I.form == FORM_UNREDUCED)
-            for (int o = lane; o < 3 * Qz; o += 32) {
-                const int a = o / Qz, k = o - a * Qz;
-                double s = 0.0;
-                for (int l = 0; l < Qz; ++l) {
-                    double t = 0.0;
-                    for (int m = 0; m < I.Mz; ++m) t += Gp[256 + (a * QZMAX + l) * 8 + m];
-                    s = fma(I.zH[l * Qz + k], t, s);
-                }
-                Pz[a * QZMAX + k] = s;
-            }
-        __syncwarp();
-    }
-    // ---- transverse factors n Y[a][t]
-    {
-        const double n = sc[16], T = sc[13];
-        const int Qz = I.Qz;
-        for (int o = lane; o < 4 * Tc; o += 32) {
+        __syncthreads();
+        // transverse factors n Y[a][t] = A[a][0][ky] Z0(t) + A[a][1][ky] Z2(t)
+        for (int o = wid; o < 4 * Tc; o += NOD_WARPS) {
             const int a = o / Tc, t = o - a * Tc;
-            double s = 0.0;
-            for (int j = 0; j < NTERMS; ++j) {
-                if (c_mono[j][0] != a) continue;
-                const int b = c_mono[j][1], cc = c_mono[j][2];
-                double e;
-                if (I.form == FORM_UNREDUCED) {
-                    const int ky = t / Qz, kz = t - ky * Qz;
-                    e = Py[b * QYMAX + ky] * Pz[cc * QZMAX + kz];
-                } else if (I.form == FORM_REDUCED2D) {
-                    const int ky = t >> 1, slot = t & 1;
-                    e = Py[b * QYMAX + ky] * (slot == 0 ? gmom(cc, T) : gmom(cc + 2, T));
-                } else {
-                    e = t == 0 ? gmom(b, T) * gmom(cc, T) : gmom(b + 2, T) * gmom(cc, T) + gmom(b, T) * gmom(cc + 2, T);
-                }
-                s = fma(sc[j], e, s);
+            double z0, z2;
+            int ky;
+            if (I.form == FORM_UNREDUCED) {
+                ky = t / Qz;
+                const int kz = t - ky * Qz;
+                z0 = Pz[(0 * QZMAX + kz) * TILE + lane];
+                z2 = Pz[(2 * QZMAX + kz) * TILE + lane];
+            } else {
+                ky = t >> 1;
+                const bool theta = t & 1;
+                z0 = theta ? T : 1.0;
+                z2 = theta ? 3.0 * T * T : T;
             }
-            s *= n;
-            const size_t r = (size_t)(8 * Q + a * Tc + t) * ld + i;
-            I.tab[r] = s;
-            if (I.tab32) I.tab32[r] = (float)s;
+            const double s = fma(Ay[((2 * a) * Qy + ky) * TILE + lane], z0, Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2);
+            if (valid) {
+                const size_t r = (size_t)(8 * Q + a * Tc + t) * ld + i;
+                I.tab[r] = s;
+                if (I.tab32) I.tab32[r] = (float)s;
+            }
+        }
+    } else if (wid < 8) {
+        // 1D reduced (Sec. II B 1): slots phi, theta carry the (p_y, p_z) Gaussian moments
+        const int a = wid >> 1, slot = wid & 1;
+        double s = 0.0;
+        for (int j = 0; j < NTERMS; ++j) {
+            if (c_mono[j][0] != a) continue;
+            const int b = c_mono[j][1], cc = c_mono[j][2];
+            const double e = slot == 0 ? gmom(b, T) * gmom(cc, T) : gmom(b + 2, T) * gmom(cc, T) + gmom(b, T) * gmom(cc + 2, T);
+            s = fma(sc[j * TILE + lane], e, s);
+        }
+        if (valid) {
+            const size_t r = (size_t)(8 * Q + a * Tc + slot) * ld + i;
+            I.tab[r] = sc[13 * TILE + lane] * s;
+            if (I.tab32) I.tab32[r] = (float)(sc[13 * TILE + lane] * s);
         }
     }
-    if (lane == 0) {
+    if (wid == 0 && valid) {
         const size_t r = (size_t)(8 * Q + 4 * Tc) * ld + i;
-        I.tab[r] = sc[17];
-        if (I.tab32) I.tab32[r] = (float)sc[17];
+        I.tab[r] = sc[14 * TILE + lane];
+        if (I.tab32) I.tab32[r] = (float)sc[14 * TILE + lane];
     }
 }
 
@@ -880,9 +931,8 @@ cudaError_t launch_set_profiles(const Inst* d_inst, int inst, cudaStream_t s) {
 }
 
 cudaError_t launch_moments(const Inst* d_inst, const Work* d_mom, int n_mom, int buf, bool f64, bool f32, cudaStream_t s) {
-    dim3 blk(TILE, MOM_WARPS);
-    if (f64) k_moments<double><<<n_mom, blk, 0, s>>>(d_inst, d_mom, buf);
-    if (f32) k_moments<float><<<n_mom, blk, 0, s>>>(d_inst, d_mom, buf);
+    if (f64) k_moments<double><<<n_mom, TILE * MOM3_WARPS, 0, s>>>(d_inst, d_mom, buf);
+    if (f32) k_moments<float><<<n_mom, TILE * MOM3_WARPS, 0, s>>>(d_inst, d_mom, buf);
     return cudaGetLastError();
 }
 
@@ -906,22 +956,26 @@ static cudaError_t set_smem(size_t smem64, size_t smem32) {
 }
 
 cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int qmax, cudaStream_t s) {
-    static int done = 0;
-    const int wd = nodal_warp_doubles(qmax);
-    const size_t smem = (size_t)NOD_WARPS * wd * sizeof(double);
-    if (smem > 48 * 1024 && (int)smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(k_nodal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        done = (int)smem;
-    }
-    k_nodal<<<n_nod, 32 * NOD_WARPS, smem, s>>>(d_inst, d_nod, wd);
+    const size_t smem = (size_t)nodal_smem_doubles(qmax) * sizeof(double);
+    if (qmax <= 8) k_nodal<8><<<n_nod, TILE * NOD_WARPS, smem, s>>>(d_inst, d_nod);
+    else k_nodal<QMAX><<<n_nod, TILE * NOD_WARPS, smem, s>>>(d_inst, d_nod);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax) {
+    static int nodal_done = 0;
+    const int smem = nodal_smem_doubles(qmax) * (int)sizeof(double);
+    if (smem > 48 * 1024 && smem > nodal_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_nodal<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_nodal<QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        nodal_done = smem;
+    }
+    return set_smem(smem64, smem32);
 }
 
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
                           bool f64, bool f32, cudaStream_t s) {
-    cudaError_t e = set_smem(smem64, smem32);
-    if (e != cudaSuccess) return e;
     dim3 blk(TILE, UPD_WARPS);
     if (f64) k_update<double, double><<<n_upd, blk, smem64, s>>>(d_inst, d_upd, stage);
     if (f32) k_update<float, float><<<n_upd, blk, smem32, s>>>(d_inst, d_upd, stage);

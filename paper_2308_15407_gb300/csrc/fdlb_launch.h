@@ -27,6 +27,9 @@ cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int q
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
                           bool f64, bool f32, cudaStream_t s);
 
+// Shared-memory attributes of the kernels that need more than 48 KB (call outside any capture).
+cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax);
+
 // Kernel classes for the optional event timing of fdlb_profile.
 enum KernelKind : int { KK_MOMENTS = 0, KK_NODAL = 1, KK_UPDATE = 2, KK_RESID = 3, KK_COUNT = 4 };
 
