@@ -8,12 +8,17 @@ velocities 12 half-range x (6 per side) x 6 x 4 full-range = 288 per node, f sto
 FP32 with FP64 moments/closure/residual.  Synthetic (no dataset): the uniform
 equilibrium start of every instance.
 
-One bench step = CHUNK TVD-RK3 time steps of the whole batch (every row of the hot path:
-moments, chi, transport, gradients, projected Shakhov + J1 target, WENO-5 advection with
-diffuse walls, RK3 combination, per-step residual and status).  Instances that become
-non-finite (the scheme is linearly unstable at eta0 >= 0.3 for this velocity set) are
-frozen by the status logic and contribute no work; the work count uses the per-instance
-step counters, so only performed updates are counted.
+Every RK3 step runs every row of the hot path: moments, chi, transport, gradients,
+projected Shakhov + J1 target, WENO-5 advection with diffuse walls, RK3 combination,
+per-step residual and status.  Instances that become non-finite (the scheme is linearly
+unstable at eta0 >= 0.3 for this velocity set) are frozen by the status logic and do no
+further work; the work count uses the per-instance step counters, so only performed
+updates are counted.
+
+One bench step = one steady-state solve of the whole sweep from the uniform start to
+residual 1e-8 (instances freeze when they converge).  value = node-velocity updates/s
+performed over the timed solves; steady_state_solves_per_s = converged instances per second;
+plain_fp64_per_instance = one instance solved alone in FP64 storage, for comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fdlb|reference]
 
@@ -35,7 +40,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "steady-state solves/s at residual 1e-8 (batched+warm-start vs plain FP64); node-vel updates/s, % BW"
 UNIT = "node-velocity updates/s"
-CHUNK = 200                       # RK3 time steps per bench step
 ETAS = (0.1, 0.2, 0.3, 0.4)
 KNS = (0.05, 0.1, 0.5)
 WORKLOAD = "Couette sweep: 12 instances (eta0 {0.1,0.2,0.3,0.4} x Kn {0.05,0.1,0.5}), Nx=200 tanh A=1.5, walls T=1 u_y=-+0.42, 12x6x4=288 velocities, FP32 storage / FP64 moments"
@@ -191,6 +195,23 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+TOL = 1e-8            # steady-state residual of one solve
+MAX_STEPS = 200000    # per solve
+CHECK = 2000          # steps between host checks of the instance status
+
+
+def solve(s, F, nx):
+    """Reset every instance to the uniform start (n = 1, u = 0, T = 1) and solve to TOL."""
+    import numpy as np
+    for i in range(s.count):
+        s.set_profiles(i, np.ones(nx[i]), np.zeros(nx[i]), np.ones(nx[i]))
+    try:
+        s.run(TOL, MAX_STEPS, check_every=CHECK, timeout_s=600.0)
+    except F.FdlbError as e:
+        if e.code not in (F.FDLB_ENONFINITE, F.FDLB_EUNPHYSICAL):
+            raise
+
+
 def run_fdlb(args):
     import numpy as np
     import torch
@@ -215,119 +236,145 @@ def run_fdlb(args):
     params = couette_params(F, "fp32")
     stream = torch.cuda.current_stream()
     s = F.Solver(params, device=f"cuda:{local}", stream=stream)
+    nx = s.nx
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")   # 256 MB > 129 MB L2
 
-    def work_steps():
-        return s.status()[2].copy()
-
     for _ in range(args.warmup):
-        s.step(CHUNK)
+        solve(s, F, nx)
     torch.cuda.synchronize()
 
+    # ---- timed region: K full steady-state solves of the sweep
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    steps0 = work_steps()
+    updates = 0.0
+    solved = 0
+    steps_per_solve = []
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
         for j in range(args.steps):
             flush.fill_(float(j))                      # evict L2 between timed iterations (not timed)
+            torch.cuda.synchronize()
             ev[j][0].record(stream)
-            s.step(CHUNK)
+            solve(s, F, nx)                           # set_profiles (reset) + fdlb_run to TOL
             ev[j][1].record(stream)
+            _, status, done = s.status()
+            updates += float(sum(int(d) * a * b for d, a, b in zip(done, nx, s.nvel)))
+            solved += int((status == F.CONVERGED).sum())
+            steps_per_solve.append([int(d) for d in done])
         torch.cuda.synchronize()
         barrier()
-    steps1 = work_steps()
-    # Kernel durations: the same stepping with the library's per-launch CUDA events on its
-    # stream (events sit between launches, so this pass launches kernels one by one instead
-    # of replaying the step graph used above; the kernel durations are the same).
-    s.profile(True)
-    for j in range(args.steps):
-        flush.fill_(float(j))
-        s.step(CHUNK)
-    prof = s.profile_read()
-    s.profile(False)
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    done = steps1 - steps0
-    updates = float(sum(int(d) * nx * nv for d, nx, nv in zip(done, s.nx, s.nvel)))
-    t = torch.tensor([ms, updates], dtype=torch.float64, device=f"cuda:{local}")
+    t = torch.tensor([ms, updates, float(solved)], dtype=torch.float64, device=f"cuda:{local}")
     if dist is not None:
         tm = t[:1].clone()
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         tu = t[1:].clone()
         dist.all_reduce(tu, op=dist.ReduceOp.SUM)
-        ms_max, updates_all = float(tm.item()), float(tu.item())
+        ms_max, updates_all, solved_all = float(tm.item()), float(tu[0].item()), float(tu[1].item())
     else:
-        ms_max, updates_all = ms, updates
+        ms_max, updates_all, solved_all = ms, updates, float(solved)
     value = updates_all / (ms_max * 1e-3)
+    solves_per_s = solved_all / (ms_max * 1e-3)
+    _, status, _ = s.status()
 
-    # ---- roofline of the dominant kernel class (event timing on the solver's stream)
+    # ---- kernel durations: 2000 steps of the sweep with the library's per-launch CUDA events
+    # on its stream (launches one by one instead of replaying the step graph; same kernels)
+    for i in range(s.count):
+        s.set_profiles(i, np.ones(nx[i]), np.zeros(nx[i]), np.ones(nx[i]))
+    s.step(600)                                        # past the start-up transient
+    st0 = s.status()[2].copy()
+    s.profile(True)
+    s.step(2000)
+    prof = s.profile_read()
+    s.profile(False)
+    pdone = s.status()[2] - st0
     total_kernel_ms = sum(v[0] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
-    # average per-instance work per launch, counting only instances that advanced
-    active = [i for i in range(len(params)) if done[i] > 0]
-    flops = 0.0
-    for i in active:
-        per = kernel_flops(dom, params[i], s.nx[i], s.nvel[i])
-        # launches of the class per time step: moments 3, nodal 3, update 3, resid 1
-        flops += per * done[i] * {"moments": 3, "nodal": 3, "update": 3, "resid": 1}[dom]
-    launches_per_step = {"moments": 3, "nodal": 3, "update": 3, "resid": 1}[dom]
-    steps_timed = args.steps * CHUNK          # the profiled pass takes as many steps
-    flops_per_launch = flops / max(1, steps_timed * launches_per_step)
+    per_step_launches = {"moments": 3, "nodal": 3, "update": 3, "resid": 1}[dom]
+    flops = sum(kernel_flops(dom, params[i], nx[i], s.nvel[i]) * int(pdone[i]) for i in range(len(params)))
+    flops_per_launch = flops / max(1, 2000 * per_step_launches)
     avg_launch_s = dom_ms * 1e-3 / max(1, dom_launches)
     fp32_dom = dom == "update"
     peak = FP32_PEAK_TFLOPS if fp32_dom else FP64_PEAK_TFLOPS
     achieved = flops_per_launch / avg_launch_s / 1e12
     roofline = {"bound": "alu", "kernel": {"update": "k_update<float,float>", "moments": "k_moments<float>",
-                                           "nodal": "k_nodal", "resid": "k_resid"}[dom],
+                                           "nodal": "k_nodal<8>", "resid": "k_resid"}[dom],
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": ("nominal FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz" if fp32_dom else
                                 "nominal FP64 1.25 TFLOP/s (profiling recipe; FMA probe measured 1.22)"),
                 "share": dom_ms / total_kernel_ms if total_kernel_ms else None,
-                "kernel_ms": {k: v[0] for k, v in prof.items()}}
-    gpu_launches = sum(v[1] for v in prof.values())
+                "kernel_ms_per_step": {k: v[0] / 2000 for k, v in prof.items()},
+                "measured_over": "2000 RK3 steps of the sweep after 600 start-up steps, per-launch CUDA events"}
+    # launches in the timed region: per solve, 4 per instance for the reset (profiles x2,
+    # moments, residual anchor) and 10 per RK3 step of the batch until the last instance stops
+    # (fdlb_run advances in chunks of CHECK steps)
+    gpu_launches = sum(4 * s.count + 10 * CHECK * math.ceil(max(x) / CHECK) for x in steps_per_solve)
 
-    # ---- e2e: through the public API with host buffers every step
+    # ---- e2e: through the public API with host buffers, one solve
     e2e = None
-    if rank == 0 or world > 1:
-        nx = s.nx
-        prof_h2d = sum(4 * ((n + 31) // 32 * 32) * 8 for n in nx)
-        x = [np.linspace(-0.5, 0.5, n) for n in nx]
-        e_times = []
-        e_updates = 0.0
-        for j in range(max(1, min(args.steps, 3))):
-            flush.fill_(float(j))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for i in range(len(params)):
-                s.set_profiles(i, np.ones(nx[i]), 0.84 * x[i], np.ones(nx[i]))       # host -> device
-            st0 = s.status()[2].copy()
-            s.step(CHUNK)
-            outs = [s.moments(i) for i in range(len(params))]                       # device -> host
-            st1 = s.status()[2].copy()
-            e_times.append(time.perf_counter() - t0)
-            e_updates += float(sum(int(d) * a * b for d, a, b in zip(st1 - st0, s.nx, s.nvel)))
-        e2e = {"value": e_updates / sum(e_times), "unit": UNIT,
-               "h2d_bytes_per_step": int(prof_h2d), "d2h_bytes_per_step": int(sum(8 * 8 * n for n in nx))}
+    if rank == 0:
+        xg = [np.linspace(-0.5, 0.5, n) for n in nx]
+        flush.fill_(0.5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(s.count):
+            s.set_profiles(i, np.ones(nx[i]), np.zeros(nx[i]), np.ones(nx[i]))          # host -> device
+        try:
+            s.run(TOL, MAX_STEPS, check_every=CHECK, timeout_s=600.0)
+        except F.FdlbError as e:
+            if e.code not in (F.FDLB_ENONFINITE, F.FDLB_EUNPHYSICAL):
+                raise
+        outs = [s.moments(i) for i in range(s.count)]                                  # device -> host
+        el = time.perf_counter() - t0
+        _, st_e, done_e = s.status()
+        e2e = {"value": float(sum(int(d) * a * b for d, a, b in zip(done_e, nx, s.nvel))) / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(4 * ((n + 31) // 32 * 32) * 8 for n in nx)),
+               "d2h_bytes_per_step": int(sum(8 * 8 * n for n in nx)),
+               "solves_per_s": float((st_e == F.CONVERGED).sum()) / el}
+
+    # ---- plain FP64 per-instance solver: one instance of the sweep alone (eta0 = 0.1, Kn = 0.5)
+    plain = None
+    if rank == 0:
+        p64 = F.Params(nx=200, qx_half=6, qy=6, qz=4, kn=0.5, eta0=0.1, U_left=-0.42, U_right=0.42, grid="tanh",
+                       stretch=1.5, flow=F.COUETTE, precision="fp64")
+        s64 = F.Solver([p64], device=f"cuda:{local}", stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.run(TOL, MAX_STEPS, check_every=CHECK, timeout_s=600.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        n64 = int(s64.status()[2][0])
+        plain = {"solves_per_s": 1.0 / sec, "steps": n64, "seconds": sec,
+                 "node_vel_updates_per_s": n64 * s64.nx[0] * s64.nvel[0] / sec,
+                 "instance": "eta0=0.1, Kn=0.5, FP64 storage, alone in its context"}
+        s64.close()
 
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1:
         r = oracle_rate(seconds_target=12.0)
         cpu = {"value": r["rate"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{r['steps']} RK3 steps of one instance (eta0=0.1, Kn=0.1; 200 nodes x 288 velocities), FP64 numpy oracle, single thread"}
+               "sample": f"{r['steps']} RK3 steps of one instance of the sweep (eta0=0.1, Kn=0.1; 200 nodes x 288 velocities), FP64 numpy oracle, single thread"}
 
     if rank == 0:
-        _, status, nsteps = s.status()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "instances_per_gpu": len(params), "time_steps_per_bench_step": CHUNK,
+            "config": {"workload": WORKLOAD, "instances_per_gpu": len(params),
+                       "bench_step": f"one steady-state solve of the sweep from the uniform start to residual {TOL:g} (per-instance freezing)",
                        "precision": "f stored/advected in FP32; moments, closure, projections, residual FP64",
                        "l2": "flushed between timed iterations (256 MB write)",
+                       "instances_converged_per_solve": int(solved / max(1, args.steps)),
                        "instances_failed_nonfinite": int((status == F.FAILED_NONFINITE).sum()),
+                       "rk3_steps_per_instance_last_solve": steps_per_solve[-1] if steps_per_solve else None,
                        "parallelism": f"instance replicas x{world}"},
+            "steady_state_solves_per_s": solves_per_s,
+            "plain_fp64_per_instance": plain,
+            "solves_per_s_vs_plain_fp64": (solves_per_s / plain["solves_per_s"]) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
             "clocks": clk.summary(),
         }
@@ -339,7 +386,7 @@ def run_fdlb(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fdlb", choices=["fdlb", "reference"])
     args = ap.parse_args()
