@@ -21,6 +21,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -245,7 +247,7 @@ void ortho_values(int L, const std::vector<double>& alpha, const std::vector<dou
     }
 }
 
-Rule make_rule(int kind, int Q) {
+Rule make_rule_uncached(int kind, int Q) {
     Rule r;
     if (kind == 0) {
         half_range_recurrence(Q + 1, r.alpha, r.beta);
@@ -264,6 +266,19 @@ Rule make_rule(int kind, int Q) {
         for (int l = 0; l < Q; ++l) s += h[l] * h[l];
         r.w[k] = (double)(1.0 / s);
     }
+    return r;
+}
+
+// Rules depend only on (kind, Q): cache them (large batches repeat a few orders).
+Rule make_rule(int kind, int Q) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, Rule> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(kind, Q);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    Rule r = make_rule_uncached(kind, Q);
+    cache.emplace(key, r);
     return r;
 }
 
@@ -316,12 +331,22 @@ int validate(const fdlb_params& p, std::string& why) {
 // Byte layout of one instance inside the workspace.
 struct Layout {
     size_t tables = 0, fbuf = 0, node = 0, tab = 0, tab32 = 0, misc = 0, msum = 0, mcnt = 0, total = 0;
-    int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0;
+    int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0, groups = 1;
 };
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-Layout layout_of(const fdlb_params& p) {
+// Blocks per tile of the moment reduction: enough blocks to fill the GPU for small batches,
+// one block per tile (no partial buffer) for large ones.
+int mom_groups(const std::vector<fdlb_params>& ps) {
+    long tiles = 0;
+    int qmax = 1;
+    for (auto& p : ps) { tiles += (p.nx + TILE - 1) / TILE; qmax = std::max(qmax, (int)p.qx_half); }
+    long g = (2048 + tiles - 1) / tiles;
+    return (int)std::max(1L, std::min<long>(g, 2 * qmax));
+}
+
+Layout layout_of(const fdlb_params& p, int groups) {
     Layout L;
     L.form = p.qz > 0 ? FORM_UNREDUCED : (p.qy > 0 ? FORM_REDUCED2D : FORM_REDUCED1D);
     L.Tc = L.form == FORM_UNREDUCED ? p.qy * p.qz : (L.form == FORM_REDUCED2D ? 2 * p.qy : 2);
@@ -352,7 +377,8 @@ Layout layout_of(const fdlb_params& p) {
     L.tab = al256((size_t)L.ntab * L.ld * 8);
     L.misc = al256(8 * 8);
     L.tab32 = p.precision == FDLB_FP32_STORAGE ? al256((size_t)L.ntab * L.ld * 4) : 0;
-    L.msum = al256((size_t)2 * p.qx_half * MOM_SUMS * L.ld * 8);
+    L.groups = std::min(groups, 2 * p.qx_half);
+    L.msum = L.groups > 1 ? al256((size_t)L.groups * MOM_SUMS * L.ld * 8) : 0;
     L.mcnt = al256((size_t)(L.ld / TILE) * 4);
     L.total = L.tables + 3 * L.fbuf + L.node + L.tab + L.tab32 + L.misc + L.msum + L.mcnt;
     return L;
@@ -363,14 +389,22 @@ size_t global_bytes(int count, int n_mom, int n_upd, int n_nod) {
            al256(sizeof(int) * count) + al256(sizeof(long long) * count) + al256(sizeof(double) * count);
 }
 
-const int KC = 32;   // velocities per update work item
+// Velocities per update block: small batches split a tile's velocities into chunks of 32 to
+// occupy the GPU; large batches give a block the whole tile (the node table is loaded once).
+int upd_chunk(const std::vector<fdlb_params>& ps) {
+    long tiles = 0;
+    for (auto& p : ps) tiles += (p.nx + TILE - 1) / TILE;
+    return tiles >= 1216 ? 1 << 20 : 32;
+}
 
 void count_work(const std::vector<fdlb_params>& p, int& n_mom, int& n_upd, int& n_nod) {
     n_mom = n_upd = n_nod = 0;
+    const int G = mom_groups(p);
     for (auto& q : p) {
-        Layout L = layout_of(q);
+        Layout L = layout_of(q, G);
         int tiles = (q.nx + TILE - 1) / TILE;
-        n_mom += tiles * 2 * q.qx_half;
+        n_mom += tiles * L.groups;
+        const int KC = std::min(L.K, upd_chunk(p));
         n_upd += tiles * ((L.K + KC - 1) / KC);
         n_nod += tiles * 3;
     }
@@ -395,7 +429,8 @@ extern "C" size_t fdlb_workspace_bytes(const fdlb_params* params, int32_t count)
     int n_mom, n_upd, n_nod;
     count_work(p, n_mom, n_upd, n_nod);
     size_t tot = global_bytes(count, n_mom, n_upd, n_nod);
-    for (auto& q : p) tot += layout_of(q).total;
+    const int G = mom_groups(p);
+    for (auto& q : p) tot += layout_of(q, G).total;
     return tot;
 }
 
@@ -434,15 +469,17 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     std::vector<std::pair<size_t, size_t>> regions;   // (offset, size) of table regions
     size_t max_smem64 = 0, max_smem32 = 0;
 
+    const int mgroups = mom_groups(c->prm);
+    const int ukc = upd_chunk(c->prm);
     for (int ii = 0; ii < count; ++ii) {
         const fdlb_params& p = c->prm[ii];
-        Layout L = layout_of(p);
+        Layout L = layout_of(p, mgroups);
         const int Q = p.qx_half, N = p.nx;
         Inst I;
         std::memset(&I, 0, sizeof(I));
         I.N = N; I.ld = L.ld; I.Q = Q; I.Qy = p.qy; I.Qz = p.qz; I.form = L.form; I.Tc = L.Tc; I.K = L.K;
         I.Mx = MX; I.My = L.My; I.Mz = L.Mz;
-        I.precision = p.precision; I.j1_shear = p.j1_shear; I.ntab = L.ntab;
+        I.precision = p.precision; I.j1_shear = p.j1_shear; I.ntab = L.ntab; I.mgroups = L.groups;
         I.kn = p.kn; I.eta0 = p.eta0; I.chi0 = chi_cs(p.eta0);
         I.mu0c = (5.0 / 16.0) * std::sqrt(2.0 * M_PI) * I.chi0 * p.kn;
         I.accel_y = p.accel_y;
@@ -630,7 +667,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         I.tab = reinterpret_cast<double*>(take(L.tab));
         I.tab32 = L.tab32 ? reinterpret_cast<float*>(take(L.tab32)) : nullptr;
         I.misc = reinterpret_cast<double*>(take(L.misc));
-        I.msum = reinterpret_cast<double*>(take(L.msum));
+        I.msum = L.msum ? reinterpret_cast<double*>(take(L.msum)) : nullptr;
         I.mcnt = reinterpret_cast<int*>(take(L.mcnt));
         counters.push_back({I.mcnt, L.mcnt});
         I.status = c->d_status_all + ii;
@@ -639,7 +676,8 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
 
         int tiles = (N + TILE - 1) / TILE;
         for (int t = 0; t < tiles; ++t) {
-            for (int kx = 0; kx < 2 * Q; ++kx) wm.push_back({ii, t * TILE, kx, t});
+            for (int g = 0; g < L.groups; ++g) wm.push_back({ii, t * TILE, g, t});
+            const int KC = std::min(L.K, ukc);
             for (int k0 = 0; k0 < L.K; k0 += KC) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + KC)});
             for (int role = 0; role < 3; ++role) wn.push_back({ii, t * TILE, role, 0});
         }

@@ -38,7 +38,7 @@ struct Inst {
     int Mx, My, Mz;
     int precision, j1_shear, pad0;
     int ntab;                  // doubles per node in the projection table
-    int pad1;
+    int mgroups;               // x-velocity groups of the moment reduction (blocks per tile)
     double kn, eta0, chi0, mu0c, dt, ds, accel_y;
     double T_L, T_R, U_L, U_R, T_init;
     double x_h0;               // h_0 of the half-range orthonormal family
@@ -85,7 +85,7 @@ struct Inst {
     double* node;              // [NROWS*ld]
     double* tab;               // [ntab*ld] projection table (see below)
     double* misc;              // [NMISC]
-    double* msum;              // [2Q][14][ld] per-x-velocity partial raw moment sums
+    double* msum;              // [mgroups][14][ld] partial raw moment sums (mgroups > 1 only)
     int* mcnt;                 // [tiles] arrival tickets of the moment CTAs of a tile (zero between uses)
     int* status;
     long long* steps;

@@ -295,80 +295,16 @@ struct InnerSum<float> {
 };
 
 // Per node: the 14 raw sums over all velocities, factorised as sum_kx px^a (sum_t w_j(t) f).
-// One block per (instance, 32-node tile, x-velocity kx); its 4 warps split the transverse index.
-// Each block writes its 14 partial sums for kx; the last block of a tile to arrive (ticket from
-// an atomic counter) adds the 2Q partials in kx order -- so the result does not depend on the
-// arrival order -- converts them to n, u, T, q, Pi and resets the ticket.
+// One block per (instance, 32-node tile, group of x-velocities); its 4 warps split the
+// transverse index.  With one group per tile (large batches) the block converts the sums to
+// moments itself.  With G > 1 groups (small batches, to occupy the GPU) each block writes its
+// 14 partial sums; the last block of the tile to arrive (ticket from an atomic counter) adds
+// the G partials in group order -- the result does not depend on the arrival order -- converts
+// them and resets the ticket.
 constexpr int MOM3_WARPS = 4;
 
-template <typename S>
-__global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
-    __shared__ double part[MOM3_WARPS][NTW][TILE];
-    __shared__ int last;
-    const Work w = work[blockIdx.x];
-    const Inst& I = insts[w.inst];
-    if (*I.status != FDLB_ACTIVE) return;
-    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int i = w.i0 + lane, kx = w.k0, tile = w.k1;
-    const int ld = I.ld, Tc = I.Tc, Q = I.Q;
-    const bool valid = i < I.N;
-    const S* f = static_cast<const S*>(I.f[buf]) + (size_t)kx * Tc * ld + (valid ? i : 0);
-    InnerSum<S> a[NTW];
-    for (int t = g; t < Tc; t += MOM3_WARPS) {
-        const S fv = valid ? f[(size_t)t * ld] : (S)0;
-#pragma unroll
-        for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], I.twh[j * Tc + t], I.twl[j * Tc + t]);
-    }
-#pragma unroll
-    for (int j = 0; j < NTW; ++j) part[g][j][lane] = a[j].value();
-    __syncthreads();
-    if (g == 0) {
-        double S6[NTW];
-#pragma unroll
-        for (int j = 0; j < NTW; ++j) {
-            double v = 0.0;
-            for (int q = 0; q < MOM3_WARPS; ++q) v += part[q][j][lane];
-            S6[j] = v;
-        }
-        const double p = I.px[kx], p2 = p * p, p3 = p2 * p;
-        // 0 n, 1 sneg, 2 spos, 3 sy, 4 sxx, 5 sxy, 6 syy, 7 se, 8 sxxx, 9 sxyy, 10 sxxy, 11 syyy, 12 sxe, 13 sye
-        double o[MOM_SUMS];
-        o[0] = S6[0];
-        o[1] = kx >= Q ? p * S6[0] : 0.0;
-        o[2] = kx >= Q ? 0.0 : p * S6[0];
-        o[3] = S6[1];
-        o[4] = p2 * S6[0];
-        o[5] = p * S6[1];
-        o[6] = S6[2];
-        o[7] = S6[4];
-        o[8] = p3 * S6[0];
-        o[9] = p * S6[2];
-        o[10] = p2 * S6[1];
-        o[11] = S6[3];
-        o[12] = p * S6[4];
-        o[13] = S6[5];
-        double* dst = I.msum + (size_t)kx * MOM_SUMS * ld + i;
-        if (valid)
-#pragma unroll
-            for (int j = 0; j < MOM_SUMS; ++j) dst[(size_t)j * ld] = o[j];
-        __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(I.mcnt + tile, 1) == 2 * Q - 1;
-    __syncthreads();
-    if (!last || g != 0) return;
-    __threadfence();
-    if (threadIdx.x == 0) I.mcnt[tile] = 0;
-    if (!valid) return;
-    double s[MOM_SUMS];
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) s[j] = 0.0;
-    for (int q = 0; q < 2 * Q; ++q) {
-        const double* src = I.msum + (size_t)q * MOM_SUMS * ld + i;
-#pragma unroll
-        for (int j = 0; j < MOM_SUMS; ++j) s[j] += __ldcg(src + (size_t)j * ld);
-    }
+__device__ void finalize_moments(const Inst& I, int i, const double* s) {
+    const int ld = I.ld;
     const double n = s[0], sx = s[1] + s[2];
     const double ux = sx / n, uy = s[3] / n;
     const double Pxx = s[4] - n * ux * ux, Pxy = s[5] - n * ux * uy, Pyy = s[6] - n * uy * uy;
@@ -394,6 +330,98 @@ __global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __res
     nd[R_LNN * ld + i] = log(n);
     nd[R_LNT * ld + i] = log(T);
     nd[R_LNCHI * ld + i] = log(chi_cs(I.eta0 * n));
+}
+
+template <typename S>
+__global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
+    __shared__ double part[MOM3_WARPS][MOM_SUMS][TILE];
+    __shared__ int last;
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
+    if (*I.status != FDLB_ACTIVE) return;
+    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = w.i0 + lane, grp = w.k0, tile = w.k1;
+    const int ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
+    const int kx0 = grp * 2 * Q / G, kx1 = (grp + 1) * 2 * Q / G;
+    const bool valid = i < I.N;
+    const S* fb = static_cast<const S*>(I.f[buf]) + (valid ? i : 0);
+    // 0 n, 1 sneg, 2 spos, 3 sy, 4 sxx, 5 sxy, 6 syy, 7 se, 8 sxxx, 9 sxyy, 10 sxxy, 11 syyy, 12 sxe, 13 sye
+    double o[MOM_SUMS];
+#pragma unroll
+    for (int j = 0; j < MOM_SUMS; ++j) o[j] = 0.0;
+    // warps own whole x-velocities when the block has at least as many as warps (the FP64 outer
+    // sums then run once per x-velocity); otherwise they split the transverse index
+    const bool by_kx = kx1 - kx0 >= MOM3_WARPS;
+    const int kxs = by_kx ? kx0 + g : kx0, kxstep = by_kx ? MOM3_WARPS : 1;
+    const int t0 = by_kx ? 0 : g, tstep = by_kx ? 1 : MOM3_WARPS;
+    for (int kx = kxs; kx < kx1; kx += kxstep) {
+        InnerSum<S> a[NTW];
+        const S* f = fb + (size_t)kx * Tc * ld;
+        for (int t = t0; t < Tc; t += tstep) {
+            const S fv = valid ? f[(size_t)t * ld] : (S)0;
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], I.twh[j * Tc + t], I.twl[j * Tc + t]);
+        }
+        const double S0 = a[0].value(), S1 = a[1].value(), S2 = a[2].value(), S3 = a[3].value();
+        const double S4 = a[4].value(), S5 = a[5].value();
+        const double p = I.px[kx], p2 = p * p, p3 = p2 * p;
+        o[0] += S0;
+        if (kx >= Q) o[1] = fma(p, S0, o[1]); else o[2] = fma(p, S0, o[2]);
+        o[3] += S1;
+        o[4] = fma(p2, S0, o[4]);
+        o[5] = fma(p, S1, o[5]);
+        o[6] += S2;
+        o[7] += S4;
+        o[8] = fma(p3, S0, o[8]);
+        o[9] = fma(p, S2, o[9]);
+        o[10] = fma(p2, S1, o[10]);
+        o[11] += S3;
+        o[12] = fma(p, S4, o[12]);
+        o[13] += S5;
+    }
+#pragma unroll
+    for (int j = 0; j < MOM_SUMS; ++j) part[g][j][lane] = o[j];
+    __syncthreads();
+    if (G == 1) {
+        if (g != 0 || !valid) return;
+        double s[MOM_SUMS];
+#pragma unroll
+        for (int j = 0; j < MOM_SUMS; ++j) {
+            double v = 0.0;
+            for (int q = 0; q < MOM3_WARPS; ++q) v += part[q][j][lane];
+            s[j] = v;
+        }
+        finalize_moments(I, i, s);
+        return;
+    }
+    if (g == 0) {
+        double* dst = I.msum + (size_t)grp * MOM_SUMS * ld + i;
+        if (valid)
+#pragma unroll
+            for (int j = 0; j < MOM_SUMS; ++j) {
+                double v = 0.0;
+                for (int q = 0; q < MOM3_WARPS; ++q) v += part[q][j][lane];
+                dst[(size_t)j * ld] = v;
+            }
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(I.mcnt + tile, 1) == G - 1;
+    __syncthreads();
+    if (!last || g != 0) return;
+    __threadfence();
+    if (threadIdx.x == 0) I.mcnt[tile] = 0;
+    if (!valid) return;
+    double s[MOM_SUMS];
+#pragma unroll
+    for (int j = 0; j < MOM_SUMS; ++j) s[j] = 0.0;
+    for (int q = 0; q < G; ++q) {
+        const double* src = I.msum + (size_t)q * MOM_SUMS * ld + i;
+#pragma unroll
+        for (int j = 0; j < MOM_SUMS; ++j) s[j] += __ldcg(src + (size_t)j * ld);
+    }
+    finalize_moments(I, i, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -495,8 +523,8 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
             if (role && (a & 1)) s = -s;
             if (valid) {
                 const size_t r = (size_t)(a * 2 * Q + role * Q + k) * ld + i;
-                I.tab[r] = s;
                 if (I.tab32) I.tab32[r] = (float)s;
+                else I.tab[r] = s;
             }
         }
         return;
@@ -628,8 +656,8 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
             const double s = fma(Ay[((2 * a) * Qy + ky) * TILE + lane], z0, Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2);
             if (valid) {
                 const size_t r = (size_t)(8 * Q + a * Tc + t) * ld + i;
-                I.tab[r] = s;
                 if (I.tab32) I.tab32[r] = (float)s;
+                else I.tab[r] = s;
             }
         }
     } else if (wid < 8) {
@@ -644,14 +672,14 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
         }
         if (valid) {
             const size_t r = (size_t)(8 * Q + a * Tc + slot) * ld + i;
-            I.tab[r] = sc[13 * TILE + lane] * s;
             if (I.tab32) I.tab32[r] = (float)(sc[13 * TILE + lane] * s);
+            else I.tab[r] = sc[13 * TILE + lane] * s;
         }
     }
     if (wid == 0 && valid) {
         const size_t r = (size_t)(8 * Q + 4 * Tc) * ld + i;
-        I.tab[r] = sc[14 * TILE + lane];
         if (I.tab32) I.tab32[r] = (float)sc[14 * TILE + lane];
+        else I.tab[r] = sc[14 * TILE + lane];
     }
 }
 

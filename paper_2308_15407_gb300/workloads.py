@@ -1,0 +1,52 @@
+"""Seeded synthetic workloads (parameter sets only; no arithmetic of the method).
+
+Used by the tests and the benchmark to build identical inputs for the CUDA path and for the
+oracle.  Each function returns a list of plain dicts with the keys of ``fdlb.Params``.
+"""
+import numpy as np
+
+FOURIER, COUETTE, POISEUILLE = 0, 1, 2
+
+
+def couette_sweep(precision="fp32"):
+    """Couette flow: Nx = 200 tanh-stretched (A = 1.5), walls at T = 1 moving at -0.42/+0.42,
+    eta0 in {0.1, 0.2, 0.3, 0.4} x Kn in {0.05, 0.1, 0.5}, 6 half-range per side x 6 x 4."""
+    return [dict(nx=200, qx_half=6, qy=6, qz=4, kn=kn, eta0=eta, U_left=-0.42, U_right=0.42, grid="tanh",
+                 stretch=1.5, flow=COUETTE, precision=precision)
+            for eta in (0.1, 0.2, 0.3, 0.4) for kn in (0.05, 0.1, 0.5)]
+
+
+def fourier_5000():
+    """Fourier flow, Nx = 50 uniform, walls 0.95/1.05, eta0 = 0.1, Kn = 0.1, 4 x 4 x 4 per side."""
+    return [dict(nx=50, qx_half=4, qy=4, qz=4, kn=0.1, eta0=0.1, T_left=0.95, T_right=1.05, flow=FOURIER)]
+
+
+def batched_sweep(count=2048, seed=23084, precision="fp32"):
+    """Parameter sweep of mixed flows in one batch.  Draws, in this order per instance, from
+    numpy's PCG64(seed): flow uniform in {Fourier, Couette, Poiseuille}; Nx uniform integer in
+    [32, 512]; half-range order per side in {4, 6, 8}; log10 Kn uniform in [-2, 0]; eta0 uniform
+    in [0.01, 0.45]; Delta T uniform in [0, 0.2]; wall speed uniform in [0, 0.5]; force uniform in
+    [0, 0.1].  Every draw is made for every instance (a fixed stream); each flow uses only its
+    own parameter (Fourier: walls 1 -+ Delta T; Couette: walls at T = 1 moving -+ U; Poiseuille:
+    walls at rest, a_y).  Fourier instances use the 1D reduced velocity set (q_y = q_z = 0),
+    Couette and Poiseuille the 2D reduced set with q_y = 4; uniform grids."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        flow = int(rng.integers(0, 3))
+        nx = int(rng.integers(32, 513))
+        q = int(rng.choice([4, 6, 8]))
+        kn = float(10.0 ** rng.uniform(-2.0, 0.0))
+        eta = float(rng.uniform(0.01, 0.45))
+        dT = float(rng.uniform(0.0, 0.2))
+        uw = float(rng.uniform(0.0, 0.5))
+        ay = float(rng.uniform(0.0, 0.1))
+        p = dict(nx=nx, qx_half=q, kn=kn, eta0=eta, flow=flow, precision=precision, grid="uniform")
+        if flow == FOURIER:
+            p.update(qy=0, qz=0, T_left=1.0 - dT, T_right=1.0 + dT)
+        elif flow == COUETTE:
+            p.update(qy=4, qz=0, U_left=-uw, U_right=uw)
+        else:
+            p.update(qy=4, qz=0, accel_y=ay)
+        out.append(p)
+    return out
