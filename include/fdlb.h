@@ -188,6 +188,35 @@ int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* la
 int fdlb_step_noalloc(const fdlb_params* params, void* dev_f, size_t f_bytes, int64_t nsteps,
                       double* dev_moments, void* stream);
 
+/* ---- Learned warm start (no counterpart in the paper): a multilayer perceptron that
+ * predicts steady profiles from channel parameters, run on the tcgen05 tensor cores (BF16
+ * operands, FP32 accumulation; FP32 master weights, Adam).  16 inputs (features, zero
+ * padded), 4 hidden layers of 128 GELU units, 3 outputs.  Parameters are one flat FP32
+ * vector (fdlb_mlp_param_count values) in the order W1 [16 x 128], b1, W2 [128 x 128], b2,
+ * W3, b3, W4, b4, W5 [128 x 16] (columns 3..15 unused, kept zero), b5 [16]; W_l is stored
+ * [inputs][outputs].  Inputs: device FP32 [points][16]; targets and predictions: device
+ * FP32 [points][3].  The caller owns the workspace (fdlb_mlp_workspace_bytes(max_points)
+ * bytes, 256-byte aligned); all work is enqueued on `stream`; calls returning host data
+ * synchronise it.  FDLB_ETIMEOUT reports a tensor-core completion wait that gave up. */
+typedef struct fdlb_mlp fdlb_mlp;
+int32_t fdlb_mlp_param_count(void);
+size_t fdlb_mlp_workspace_bytes(int32_t max_points);
+const char* fdlb_mlp_last_error(const fdlb_mlp* h);
+/* Glorot-uniform weights from a counter-based hash of `seed`, zero biases, zero Adam state. */
+int fdlb_mlp_create(fdlb_mlp** out, void* dev_workspace, size_t bytes, int32_t max_points, uint64_t seed, void* stream);
+void fdlb_mlp_destroy(fdlb_mlp* h);
+int fdlb_mlp_get_params(fdlb_mlp* h, float* host_params);
+int fdlb_mlp_set_params(fdlb_mlp* h, const float* host_params);      /* also resets Adam state */
+/* Forward pass: dev_y[points][3] = network(dev_x[points][16]). */
+int fdlb_mlp_predict(fdlb_mlp* h, const float* dev_x, int32_t points, float* dev_y);
+/* One training step on points <= max_points samples: loss = mean over points and the 3
+ * outputs of (prediction - target)^2; gradient by backpropagation; Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8) with learning rate lr (lr = 0: gradient only, no update).  dev_grad
+ * (device FP32 [param_count], may be NULL) receives the gradient; host_loss (may be NULL) the
+ * loss before the update. */
+int fdlb_mlp_train_step(fdlb_mlp* h, const float* dev_x, const float* dev_y, int32_t points, float lr,
+                        float* dev_grad, double* host_loss);
+
 /* Host-only: the library's own Gauss rules (for checking the tables; no GPU needed).
  * kind 0 = half-range Gauss-Hermite on [0, inf) (Sec. III A 2), kind 1 = full-range (App. A);
  * weights are normalised to the weight omega(p) = exp(-p^2/2)/sqrt(2 pi).  nodes/weights

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdlb.so")
-SOURCES = ["fdlb_host.cpp", "fdlb_kernels.cu", "fdlb_noalloc.cu"]
+SOURCES = ["fdlb_host.cpp", "fdlb_kernels.cu", "fdlb_noalloc.cu", "fdlb_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

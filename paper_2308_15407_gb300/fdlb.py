@@ -100,6 +100,15 @@ def load() -> C.CDLL:
         "fdlb_set_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
         "fdlb_quadrature": (C.c_int, [C.c_int32, C.c_int32, dp, dp]),
         "fdlb_step_noalloc": (C.c_int, [P, vp, C.c_size_t, C.c_int64, dp, vp]),
+        "fdlb_mlp_param_count": (C.c_int32, []),
+        "fdlb_mlp_workspace_bytes": (C.c_size_t, [C.c_int32]),
+        "fdlb_mlp_last_error": (C.c_char_p, [vp]),
+        "fdlb_mlp_create": (C.c_int, [C.POINTER(vp), vp, C.c_size_t, C.c_int32, C.c_uint64, vp]),
+        "fdlb_mlp_destroy": (None, [vp]),
+        "fdlb_mlp_get_params": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "fdlb_mlp_set_params": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "fdlb_mlp_predict": (C.c_int, [vp, vp, C.c_int32, vp]),
+        "fdlb_mlp_train_step": (C.c_int, [vp, vp, vp, C.c_int32, C.c_float, vp, dp]),
         "fdlb_profile": (C.c_int, [vp, C.c_int32]),
         "fdlb_profile_read": (C.c_int, [vp, C.c_int32, dp, lp]),
     }
@@ -252,3 +261,69 @@ class Solver:
     def set_state(self, inst: int, state: bytes):
         buf = C.create_string_buffer(state, len(state))
         self._check(self.lib.fdlb_set_state(self.ctx, inst, buf, len(state)))
+
+
+class MLP:
+    """Warm-start network (tcgen05 BF16 kernels with FP32 accumulation) in a device workspace."""
+
+    NIN, NOUT = 16, 3
+
+    def __init__(self, max_points: int, seed: int = 1, device="cuda", stream=None):
+        import torch
+        self.lib = load()
+        self.max_points = int(max_points)
+        self.device = torch.device(device)
+        nb = self.lib.fdlb_mlp_workspace_bytes(self.max_points)
+        self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h = C.c_void_p()
+        rc = self.lib.fdlb_mlp_create(C.byref(self.h), C.c_void_p(ptr), nb, self.max_points, int(seed),
+                                      C.c_void_p(self.stream.cuda_stream))
+        if rc != FDLB_OK:
+            raise FdlbError(rc, self.lib.fdlb_mlp_last_error(None).decode())
+        self.nparam = self.lib.fdlb_mlp_param_count()
+
+    def _check(self, rc):
+        if rc < 0:
+            raise FdlbError(rc, self.lib.fdlb_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            self.lib.fdlb_mlp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparam, dtype=np.float32)
+        self._check(self.lib.fdlb_mlp_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        self._check(self.lib.fdlb_mlp_set_params(self.h, theta.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def predict(self, x):
+        """x: float32 device tensor [P, 16] -> float32 device tensor [P, 3]."""
+        import torch
+        x = x.contiguous()
+        y = torch.empty((x.shape[0], self.NOUT), dtype=torch.float32, device=x.device)
+        self._check(self.lib.fdlb_mlp_predict(self.h, C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(y.data_ptr())))
+        return y
+
+    def train_step(self, x, y, lr: float, want_grad: bool = False):
+        """One Adam step (lr = 0: gradient only).  Returns (loss before the step, gradient or None)."""
+        import torch
+        x = x.contiguous()
+        y = y.contiguous()
+        g = torch.empty(self.nparam, dtype=torch.float32, device=x.device) if want_grad else None
+        loss = C.c_double()
+        self._check(self.lib.fdlb_mlp_train_step(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0],
+                                                 float(lr), C.c_void_p(g.data_ptr()) if g is not None else None,
+                                                 C.byref(loss)))
+        return loss.value, g
