@@ -50,3 +50,18 @@ def batched_sweep(count=2048, seed=23084, precision="fp32"):
             p.update(qy=4, qz=0, accel_y=ay)
         out.append(p)
     return out
+
+
+def couette_family(count, seed, nx=200, qx_half=6, qy=6, qz=4, grid="tanh", precision="fp32",
+                   eta=(0.05, 0.25), log10_kn=(-1.5, -0.3), wall=(0.3, 0.5)):
+    """Couette instances with eta0, log10 Kn and wall speed U (walls at -U/+U, T = 1) drawn
+    uniformly from the given ranges by PCG64(seed), in that order per instance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        e = float(rng.uniform(*eta))
+        kn = float(10.0 ** rng.uniform(*log10_kn))
+        u = float(rng.uniform(*wall))
+        out.append(dict(nx=nx, qx_half=qx_half, qy=qy, qz=qz, kn=kn, eta0=e, U_left=-u, U_right=u, grid=grid,
+                        stretch=1.5, flow=COUETTE, precision=precision))
+    return out
