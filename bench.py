@@ -15,10 +15,12 @@ unstable at eta0 >= 0.3 for this velocity set) are frozen by the status logic an
 further work; the work count uses the per-instance step counters, so only performed
 updates are counted.
 
-One bench step = one steady-state solve of the whole sweep from the uniform start to
-residual 1e-8 (instances freeze when they converge).  value = node-velocity updates/s
-performed over the timed solves; steady_state_solves_per_s = converged instances per second;
-plain_fp64_per_instance = one instance solved alone in FP64 storage, for comparison.
+One bench step = one steady-state solve of the whole sweep to residual 1e-8 (instances
+freeze when they converge), warm-started from the profiles predicted by the warm-start
+network (trained during set-up on 36 other Couette instances the solver itself solved).
+value = node-velocity updates/s performed over the timed solves; steady_state_solves_per_s
+= converged instances per second; batched_cold_start = the same solve from the uniform
+start; plain_fp64_per_instance = one instance solved alone in FP64 storage.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fdlb|reference]
 
@@ -200,11 +202,15 @@ MAX_STEPS = 200000    # per solve
 CHECK = 2000          # steps between host checks of the instance status
 
 
-def solve(s, F, nx):
-    """Reset every instance to the uniform start (n = 1, u = 0, T = 1) and solve to TOL."""
+def solve(s, F, nx, warm=None):
+    """Reset every instance -- to the uniform start (n = 1, u = 0, T = 1), or to the local
+    equilibrium of the warm-start network's profiles -- and solve to TOL."""
     import numpy as np
-    for i in range(s.count):
-        s.set_profiles(i, np.ones(nx[i]), np.zeros(nx[i]), np.ones(nx[i]))
+    if warm is not None:
+        warm.apply(s)
+    else:
+        for i in range(s.count):
+            s.set_profiles(i, np.ones(nx[i]), np.zeros(nx[i]), np.ones(nx[i]))
     try:
         s.run(TOL, MAX_STEPS, check_every=CHECK, timeout_s=600.0)
     except F.FdlbError as e:
@@ -239,11 +245,29 @@ def run_fdlb(args):
     nx = s.nx
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")   # 256 MB > 129 MB L2
 
+    # ---- warm-start network (set-up, not timed): trained on steady states the solver produces
+    # for 36 other Couette instances of the same family (eta0 0.05-0.25, Kn 0.03-0.5, U 0.3-0.5)
+    from paper_2308_15407_gb300 import workloads
+    from paper_2308_15407_gb300.warmstart import WarmStart
+    t_setup = time.perf_counter()
+    s_train = F.Solver([F.Params(**d) for d in workloads.couette_family(36, seed=23085)], device=f"cuda:{local}", stream=stream)
+    try:
+        s_train.run(TOL, MAX_STEPS, check_every=CHECK, timeout_s=600.0)
+    except F.FdlbError as e:
+        if e.code not in (F.FDLB_ENONFINITE, F.FDLB_EUNPHYSICAL):
+            raise
+    Xtr, Ytr = WarmStart.dataset(s_train)
+    warm = WarmStart(max_points=Xtr.shape[0], seed=1, device=f"cuda:{local}")
+    hist = warm.fit(Xtr, Ytr, steps=2000)
+    s_train.close()
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+
     for _ in range(args.warmup):
-        solve(s, F, nx)
+        solve(s, F, nx, warm)
     torch.cuda.synchronize()
 
-    # ---- timed region: K full steady-state solves of the sweep
+    # ---- timed region: K full warm-started steady-state solves of the sweep
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     updates = 0.0
     solved = 0
@@ -255,7 +279,7 @@ def run_fdlb(args):
             flush.fill_(float(j))                      # evict L2 between timed iterations (not timed)
             torch.cuda.synchronize()
             ev[j][0].record(stream)
-            solve(s, F, nx)                           # set_profiles (reset) + fdlb_run to TOL
+            solve(s, F, nx, warm)                     # network profiles -> set_profiles, fdlb_run to TOL
             ev[j][1].record(stream)
             _, status, done = s.status()
             updates += float(sum(int(d) * a * b for d, a, b in zip(done, nx, s.nvel)))
@@ -333,6 +357,21 @@ def run_fdlb(args):
                "d2h_bytes_per_step": int(sum(8 * 8 * n for n in nx)),
                "solves_per_s": float((st_e == F.CONVERGED).sum()) / el}
 
+    # ---- the same batched solve from the uniform start (no warm start), once
+    cold = None
+    if rank == 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(0.25)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        solve(s, F, nx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _, st_c, done_c = s.status()
+        sec = e0.elapsed_time(e1) * 1e-3
+        cold = {"solves_per_s": float((st_c == F.CONVERGED).sum()) / sec, "seconds": sec,
+                "rk3_steps_per_instance": [int(d) for d in done_c]}
+
     # ---- plain FP64 per-instance solver: one instance of the sweep alone (eta0 = 0.1, Kn = 0.5)
     plain = None
     if rank == 0:
@@ -365,7 +404,7 @@ def run_fdlb(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "instances_per_gpu": len(params),
-                       "bench_step": f"one steady-state solve of the sweep from the uniform start to residual {TOL:g} (per-instance freezing)",
+                       "bench_step": f"one steady-state solve of the sweep to residual {TOL:g} (per-instance freezing), warm-started from the network's profiles",
                        "precision": "f stored/advected in FP32; moments, closure, projections, residual FP64",
                        "l2": "flushed between timed iterations (256 MB write)",
                        "instances_converged_per_solve": int(solved / max(1, args.steps)),
@@ -373,6 +412,10 @@ def run_fdlb(args):
                        "rk3_steps_per_instance_last_solve": steps_per_solve[-1] if steps_per_solve else None,
                        "parallelism": f"instance replicas x{world}"},
             "steady_state_solves_per_s": solves_per_s,
+            "warm_start": {"train_instances": int(len(Xtr) // 200), "train_points": int(Xtr.shape[0]),
+                           "loss_first_last": [hist[0], hist[-1]], "setup_seconds": t_setup,
+                           "network": "16 -> 4x128 GELU -> 3, tcgen05 BF16/FP32, full-batch Adam 2000 steps"},
+            "batched_cold_start": cold,
             "plain_fp64_per_instance": plain,
             "solves_per_s_vs_plain_fp64": (solves_per_s / plain["solves_per_s"]) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
