@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define FDLB_ABI_VERSION 1
+#define FDLB_ABI_VERSION 2
 
 /* Return codes. */
 #define FDLB_OK            0
@@ -66,12 +66,27 @@ extern "C" {
 #define FDLB_FP64          0   /* everything in FP64 */
 #define FDLB_FP32_STORAGE  1   /* f stored, advected and combined in FP32; moments, gradients,
                                   projections and the residual in FP64 */
+#define FDLB_FP32_THEN_FP64 2  /* two phases: FDLB_FP32_STORAGE until the per-step residual
+                                  stagnates, then FDLB_FP64 for the rest of the solve.  f is
+                                  up-cast exactly on the device at the end of the step that
+                                  detects the stagnation.  Stagnated: the residual is exactly 0,
+                                  or at the end of a window of FDLB_STAGNATION_WINDOW steps it
+                                  is not below FDLB_STAGNATION_FACTOR times its value at the
+                                  window start (windows restart after each check).  An instance
+                                  whose residual falls below freeze_tol first stays FP32.  The
+                                  workspace holds f at FP64 size from the start.  FP32 storage
+                                  cannot resolve per-step changes below half an FP32 ulp of f,
+                                  so its residual floor can lie above the requested tolerance. */
+#define FDLB_STAGNATION_WINDOW 2000
+#define FDLB_STAGNATION_FACTOR 0.9
 
 /* Per-instance status (fdlb_status). */
 #define FDLB_ACTIVE        0
 #define FDLB_CONVERGED     1
 #define FDLB_FAILED_NONFINITE  2
 #define FDLB_FAILED_UNPHYSICAL 3
+#define FDLB_STAGNATED     4   /* FDLB_FP32_STORAGE stepped with freeze_tol > 0: f stopped changing
+                                  (residual exactly 0) before the residual reached freeze_tol */
 
 /* Parameters of one channel problem.  Set struct_size = sizeof(fdlb_params). */
 typedef struct fdlb_params {
@@ -82,7 +97,7 @@ typedef struct fdlb_params {
     int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..16 (2*qx_half x-velocities) */
     int32_t  qy;          /* full-range order on y, 0 or 2..8; 0 = 1D reduced (p_y integrated out) */
     int32_t  qz;          /* full-range order on z, 0 or 3..8; 0 = (phi, theta) reduced slots */
-    int32_t  precision;   /* FDLB_FP64 | FDLB_FP32_STORAGE */
+    int32_t  precision;   /* FDLB_FP64 | FDLB_FP32_STORAGE | FDLB_FP32_THEN_FP64 */
     int32_t  j1_shear;    /* 0: J1 as printed for 2D flows; 1: add the 2 zeta_x zeta_y d_x u_y term of Eq. (j1) */
     int32_t  reserved;    /* must be 0 */
     double   stretch;     /* A of FDLB_GRID_TANH (> 0) */
@@ -133,7 +148,8 @@ int fdlb_step(fdlb_ctx* ctx, int64_t nsteps, double freeze_tol);
  * (residual < tol) or FAILED, or max_steps steps were taken, or timeout_s seconds of wall
  * time passed (FDLB_ETIMEOUT).  On stopping it returns FDLB_ENONFINITE or FDLB_EUNPHYSICAL
  * when some instance failed (the others are still advanced until they stop), else FDLB_OK
- * when all converged, or 1 when max_steps was reached with instances still active. */
+ * when all converged, 2 when all stopped but some STAGNATED, or 1 when max_steps was
+ * reached with instances still active. */
 int fdlb_run(fdlb_ctx* ctx, double tol, int64_t max_steps, int64_t check_every, double timeout_s);
 
 /* Host copy of the moments of instance `inst` (synchronises the stream):
@@ -144,12 +160,20 @@ int fdlb_moments(fdlb_ctx* ctx, int32_t inst, double* host_out);
 int fdlb_status(fdlb_ctx* ctx, double* residual, int32_t* status, int64_t* steps);
 
 /* Reset instance `inst` to the projected local equilibrium with the given profiles
- * (u_x = 0; host arrays of nx values; n > 0, T > 0) and mark it ACTIVE with 0 steps. */
+ * (u_x = 0; host arrays of nx values; n > 0, T > 0) and mark it ACTIVE with 0 steps
+ * (an FDLB_FP32_THEN_FP64 instance restarts in its FP32 phase). */
 int fdlb_set_profiles(fdlb_ctx* ctx, int32_t inst, const double* n, const double* uy, const double* T);
 
-/* Checkpoint of instance `inst`: f, step count and a parameter hash.  fdlb_state_bytes gives
- * the size; get copies device -> host (synchronises), set copies host -> device (FDLB_ESTATE
- * when the buffer belongs to other parameters). */
+/* Per-instance storage precision in use now (FDLB_FP64 or FDLB_FP32_STORAGE) and, for
+ * FDLB_FP32_THEN_FP64 instances, the step count at which f was up-cast (-1: not yet, and for
+ * the other precision forms).  Synchronises.  Either pointer may be NULL. */
+int fdlb_precision(fdlb_ctx* ctx, int32_t* storage, int64_t* switch_step);
+
+/* Checkpoint of instance `inst`: f, step count and a parameter hash (FDLB_FP32_THEN_FP64:
+ * also the storage phase and switch step; f always takes its FP64 size there, the first
+ * half holding the floats in the FP32 phase).  fdlb_state_bytes gives the size; get copies
+ * device -> host (synchronises), set copies host -> device (FDLB_ESTATE when the buffer
+ * belongs to other parameters). */
 size_t fdlb_state_bytes(const fdlb_ctx* ctx, int32_t inst);
 int fdlb_get_state(fdlb_ctx* ctx, int32_t inst, void* host, size_t bytes);
 int fdlb_set_state(fdlb_ctx* ctx, int32_t inst, const void* host, size_t bytes);
@@ -176,7 +200,7 @@ int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* la
  * Advances ONE instance (params) by nsteps RK3 steps in place: dev_f (f_bytes bytes of
  * device memory) holds its f in the layout described at the top of this file, i.e.
  * K * ceil(nx/32)*32 values of double (FDLB_FP64) or float (FDLB_FP32_STORAGE) with
- * K = 2 qx_half * T_c.  If dev_moments is not NULL it receives the 8 x nx moment rows of
+ * K = 2 qx_half * T_c (FDLB_FP32_THEN_FP64 is rejected with FDLB_EINVAL).  If dev_moments is not NULL it receives the 8 x nx moment rows of
  * the result (as fdlb_moments, device memory).  All scratch lives in one static device
  * array of FDLB_NOALLOC_SCRATCH_BYTES that every device loading the library holds until the
  * process exits; instances that need more are rejected with FDLB_ENOMEM.  The array is

@@ -316,7 +316,8 @@ int validate(const fdlb_params& p, std::string& why) {
         return bad("the 1D reduced form (qy == 0) has no y motion: walls at rest, no force");
     if (p.grid != FDLB_GRID_UNIFORM && p.grid != FDLB_GRID_TANH) return bad("unknown grid");
     if (p.grid == FDLB_GRID_TANH && !(p.stretch > 0)) return bad("stretch must be > 0");
-    if (p.precision != FDLB_FP64 && p.precision != FDLB_FP32_STORAGE) return bad("unknown precision");
+    if (p.precision != FDLB_FP64 && p.precision != FDLB_FP32_STORAGE && p.precision != FDLB_FP32_THEN_FP64)
+        return bad("unknown precision");
     if (p.j1_shear != 0 && p.j1_shear != 1) return bad("j1_shear must be 0 or 1");
     if (p.reserved != 0) return bad("reserved must be 0");
     if (!(p.kn > 0) || !std::isfinite(p.kn)) return bad("kn must be > 0");
@@ -369,14 +370,15 @@ Layout layout_of(const fdlb_params& p, int groups) {
     add(QYMAX + 2); add(QYMAX + 2);
     auto add32 = [&](size_t n) { nd += al256(n * 4) / 8; };
     add(6 * L.Tc); add32(6 * L.Tc); add32(6 * L.Tc);
-    if (p.precision == FDLB_FP32_STORAGE) { add32(2 * Q); add32(p.nx); add32(QYMAX * QYMAX); add32(L.K); add32(L.K); }
+    const bool f32 = p.precision != FDLB_FP64;             // FP32 tables (FP32 and two-phase)
+    if (f32) { add32(2 * Q); add32(p.nx); add32(QYMAX * QYMAX); add32(L.K); add32(L.K); }
     L.tables = nd * 8;
-    const size_t es = p.precision == FDLB_FP64 ? 8 : 4;
+    const size_t es = p.precision == FDLB_FP32_STORAGE ? 4 : 8;
     L.fbuf = al256((size_t)L.K * L.ld * es);
     L.node = al256((size_t)NROWS * L.ld * 8);
     L.tab = al256((size_t)L.ntab * L.ld * 8);
     L.misc = al256(8 * 8);
-    L.tab32 = p.precision == FDLB_FP32_STORAGE ? al256((size_t)L.ntab * L.ld * 4) : 0;
+    L.tab32 = f32 ? al256((size_t)L.ntab * L.ld * 4) : 0;
     L.groups = std::min(groups, 2 * p.qx_half);
     L.msum = L.groups > 1 ? al256((size_t)L.groups * MOM_SUMS * L.ld * 8) : 0;
     L.mcnt = al256((size_t)(L.ld / TILE) * 4);
@@ -479,7 +481,9 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         std::memset(&I, 0, sizeof(I));
         I.N = N; I.ld = L.ld; I.Q = Q; I.Qy = p.qy; I.Qz = p.qz; I.form = L.form; I.Tc = L.Tc; I.K = L.K;
         I.Mx = MX; I.My = L.My; I.Mz = L.Mz;
-        I.precision = p.precision; I.j1_shear = p.j1_shear; I.ntab = L.ntab; I.mgroups = L.groups;
+        I.precision = p.precision == FDLB_FP64 ? FDLB_FP64 : FDLB_FP32_STORAGE;
+        I.two_phase = p.precision == FDLB_FP32_THEN_FP64;
+        I.j1_shear = p.j1_shear; I.ntab = L.ntab; I.mgroups = L.groups;
         I.kn = p.kn; I.eta0 = p.eta0; I.chi0 = chi_cs(p.eta0);
         I.mu0c = (5.0 / 16.0) * std::sqrt(2.0 * M_PI) * I.chi0 * p.kn;
         I.accel_y = p.accel_y;
@@ -638,7 +642,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
                 }
             }
         }
-        if (p.precision == FDLB_FP32_STORAGE) {
+        if (p.precision != FDLB_FP64) {
             const double* img0 = reinterpret_cast<const double*>(img.data());
             auto host_of = [&](const double* dev) { return img0 + ((const char*)dev - (base + tab_off)) / 8; };
             float* h = put32(&I.px32, 2 * Q);
@@ -683,8 +687,8 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         }
         c->qmax = std::max(c->qmax, Q);
         size_t sm = (size_t)L.ntab * TILE;
-        if (p.precision == FDLB_FP64) max_smem64 = std::max(max_smem64, sm * 8), c->any_fp64 = true;
-        else max_smem32 = std::max(max_smem32, sm * 4), c->any_fp32 = true;
+        if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, sm * 8), c->any_fp64 = true;
+        if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, sm * 4), c->any_fp32 = true;
     }
     if (off > need) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: workspace layout overflow"); }
     c->smem_upd_f64 = max_smem64;
@@ -800,16 +804,17 @@ extern "C" int fdlb_run(fdlb_ctx* c, double tol, int64_t max_steps, int64_t chec
     while (true) {
         int rc = fdlb_status(c, nullptr, st.data(), nullptr);
         if (rc) return rc;
-        bool active = false, nonfinite = false, unphys = false;
+        bool active = false, nonfinite = false, unphys = false, stagnated = false;
         for (int s : st) {
             active |= s == FDLB_ACTIVE;
             nonfinite |= s == FDLB_FAILED_NONFINITE;
             unphys |= s == FDLB_FAILED_UNPHYSICAL;
+            stagnated |= s == FDLB_STAGNATED;
         }
         if (!active || done >= max_steps) {
             if (nonfinite) return fail(c, FDLB_ENONFINITE, "an instance produced a non-finite moment");
             if (unphys) return fail(c, FDLB_EUNPHYSICAL, "an instance produced n <= 0 or T <= 0");
-            return active ? 1 : FDLB_OK;
+            return active ? 1 : (stagnated ? 2 : FDLB_OK);
         }
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > timeout_s) return fail(c, FDLB_ETIMEOUT, "fdlb_run: wall-clock limit reached");
@@ -859,11 +864,50 @@ static uint64_t param_hash(const fdlb_params& p) {
     return h;
 }
 
+// Two-phase instances add [storage i64][switch step i64] after the header and always carry f
+// at its FP64 size.
+static size_t phase_bytes(const Inst& I) { return I.two_phase ? 16 : 0; }
+
+static size_t f_bytes_of(const Inst& I) {
+    return (size_t)I.K * I.ld * (I.precision == FDLB_FP32_STORAGE && !I.two_phase ? 4 : 8);
+}
+
 extern "C" size_t fdlb_state_bytes(const fdlb_ctx* c, int32_t inst) {
     if (!c || inst < 0 || inst >= c->count) return 0;
     const Inst& I = c->inst[inst];
-    size_t es = I.precision == FDLB_FP64 ? 8 : 4;
-    return 24 + (size_t)I.K * I.ld * es;
+    return 24 + phase_bytes(I) + f_bytes_of(I);
+}
+
+// Device copies of an instance's current storage precision and switch step.
+static int read_phase(fdlb_ctx* c, int inst, int32_t* storage, int64_t* sw) {
+    const Inst& I = c->inst[inst];
+    if (!I.two_phase) {
+        *storage = I.precision;
+        *sw = -1;
+        return FDLB_OK;
+    }
+    int32_t pr = 0;
+    double swd = -1.0;
+    const char* dI = reinterpret_cast<const char*>(c->d_inst + inst);
+    int rc = cuda_check(c, cudaMemcpyAsync(&pr, dI + offsetof(Inst, precision), sizeof(pr), cudaMemcpyDeviceToHost, c->stream), "phase copy");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(&swd, I.misc + M_SWITCH, sizeof(swd), cudaMemcpyDeviceToHost, c->stream), "phase copy");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "phase synchronize");
+    *storage = pr;
+    *sw = (int64_t)swd;
+    return rc;
+}
+
+extern "C" int fdlb_precision(fdlb_ctx* c, int32_t* storage, int64_t* switch_step) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_precision: null context");
+    for (int i = 0; i < c->count; ++i) {
+        int32_t pr;
+        int64_t sw;
+        int rc = read_phase(c, i, &pr, &sw);
+        if (rc) return rc;
+        if (storage) storage[i] = pr;
+        if (switch_step) switch_step[i] = sw;
+    }
+    return FDLB_OK;
 }
 
 extern "C" int fdlb_get_state(fdlb_ctx* c, int32_t inst, void* host, size_t bytes) {
@@ -872,13 +916,22 @@ extern "C" int fdlb_get_state(fdlb_ctx* c, int32_t inst, void* host, size_t byte
     if (need == 0 || bytes < need) return fail(c, FDLB_EINVAL, "fdlb_get_state: instance out of range or buffer too small");
     const Inst& I = c->inst[inst];
     uint64_t hdr[3] = {0x46444c42u, param_hash(c->prm[inst]), 0};
+    const size_t ph = phase_bytes(I);
+    int64_t phase[2] = {0, -1};
+    if (ph) {
+        int32_t pr;
+        int rc = read_phase(c, inst, &pr, &phase[1]);
+        if (rc) return rc;
+        phase[0] = pr;
+    }
     long long st = 0;
     int rc = cuda_check(c, cudaMemcpyAsync(&st, I.steps, sizeof(st), cudaMemcpyDeviceToHost, c->stream), "state copy");
-    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(static_cast<char*>(host) + 24, I.f[0], need - 24, cudaMemcpyDeviceToHost, c->stream), "state copy");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(static_cast<char*>(host) + 24 + ph, I.f[0], need - 24 - ph, cudaMemcpyDeviceToHost, c->stream), "state copy");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "state synchronize");
     if (rc) return rc;
     hdr[2] = (uint64_t)st;
     std::memcpy(host, hdr, 24);
+    if (ph) std::memcpy(static_cast<char*>(host) + 24, phase, 16);
     return FDLB_OK;
 }
 
@@ -891,7 +944,22 @@ extern "C" int fdlb_set_state(fdlb_ctx* c, int32_t inst, const void* host, size_
     if (hdr[0] != 0x46444c42u || hdr[1] != param_hash(c->prm[inst])) return fail(c, FDLB_ESTATE, "fdlb_set_state: state belongs to other parameters");
     const Inst& I = c->inst[inst];
     long long st = (long long)hdr[2];
-    int rc = cuda_check(c, cudaMemcpyAsync(I.f[0], static_cast<const char*>(host) + 24, need - 24, cudaMemcpyHostToDevice, c->stream), "state upload");
+    const size_t ph = phase_bytes(I);
+    int rc = FDLB_OK;
+    // kept alive until the synchronisation below (the copies are asynchronous)
+    int32_t pr = 0;
+    double swd = -1.0;
+    if (ph) {
+        int64_t phase[2];
+        std::memcpy(phase, static_cast<const char*>(host) + 24, 16);
+        if (phase[0] != FDLB_FP64 && phase[0] != FDLB_FP32_STORAGE) return fail(c, FDLB_ESTATE, "fdlb_set_state: bad storage phase");
+        pr = (int32_t)phase[0];
+        swd = (double)phase[1];
+        char* dI = reinterpret_cast<char*>(c->d_inst + inst);
+        rc = cuda_check(c, cudaMemcpyAsync(dI + offsetof(Inst, precision), &pr, sizeof(pr), cudaMemcpyHostToDevice, c->stream), "state upload");
+        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.misc + M_SWITCH, &swd, sizeof(swd), cudaMemcpyHostToDevice, c->stream), "state upload");
+    }
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.f[0], static_cast<const char*>(host) + 24 + ph, need - 24 - ph, cudaMemcpyHostToDevice, c->stream), "state upload");
     if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, c->count, inst, 0.0, c->d_resid_all, c->stream), "residual kernel");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.steps, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream), "state upload");
@@ -931,7 +999,7 @@ int ctx_f_buffer(fdlb_ctx* c, int inst, void** f, size_t* bytes) {
     if (!c || inst < 0 || inst >= c->count) return fail(c, FDLB_EINVAL, "internal: bad instance");
     const Inst& I = c->inst[inst];
     *f = I.f[0];
-    *bytes = (size_t)I.K * I.ld * (I.precision == FDLB_FP64 ? 8 : 4);
+    *bytes = f_bytes_of(I);
     return FDLB_OK;
 }
 

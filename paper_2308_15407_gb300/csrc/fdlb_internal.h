@@ -29,14 +29,20 @@ enum NodeRow : int {
 };
 
 // Per-instance misc slots (doubles).
-enum Misc : int { M_NWL = 0, M_NWR, M_RESID, M_INL, M_INR, NMISC };
+// M_WIN_STEP / M_WIN_RESID: step and residual at the start of the current stagnation window
+// (M_WIN_STEP < 0: open a window at the next step); M_SWITCH: step of the FP32 -> FP64 up-cast
+// of a two-phase instance, or -1; M_MASS0: channel mass sum_i dx_i n_i at the last anchor.
+enum Misc : int { M_NWL = 0, M_NWR, M_RESID, M_INL, M_INR, M_WIN_STEP, M_WIN_RESID, M_SWITCH, M_MASS0, NMISC };
 
 // One channel problem as the kernels see it.  All pointers are device addresses
 // inside the caller's workspace.
 struct Inst {
     int N, ld, Q, Qy, Qz, form, Tc, K;
     int Mx, My, Mz;
-    int precision, j1_shear, pad0;
+    int precision;             // storage in use now: FDLB_FP64 or FDLB_FP32_STORAGE (changes once
+                               // on the device for two-phase instances)
+    int j1_shear;
+    int two_phase;             // FDLB_FP32_THEN_FP64: tables and buffers exist for both storages
     int ntab;                  // doubles per node in the projection table
     int mgroups;               // x-velocity groups of the moment reduction (blocks per tile)
     double kn, eta0, chi0, mu0c, dt, ds, accel_y;

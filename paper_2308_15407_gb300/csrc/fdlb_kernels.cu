@@ -216,6 +216,9 @@ __global__ void k_setup(Inst* insts) {
         I.misc[M_NWL] = 1.0;
         I.misc[M_NWR] = 1.0;
         I.misc[M_RESID] = CUDART_INF;
+        I.misc[M_WIN_STEP] = -1.0;
+        I.misc[M_WIN_RESID] = CUDART_INF;
+        I.misc[M_SWITCH] = -1.0;
         *I.status = FDLB_ACTIVE;
         *I.steps = 0;
     }
@@ -232,7 +235,19 @@ __global__ void k_setup(Inst* insts) {
 template <typename S>
 __global__ void k_profiles(Inst* insts, int inst) {
     Inst& I = insts[inst < 0 ? blockIdx.x : inst];
-    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    if (I.two_phase) {
+        // a two-phase instance restarts in its FP32 phase: the FP64 launch (first in stream
+        // order) resets the phase, the FP32 launch writes f
+        if (sizeof(S) == 8) {
+            if (threadIdx.x == 0) {
+                I.precision = FDLB_FP32_STORAGE;
+                I.misc[M_SWITCH] = -1.0;
+            }
+            return;
+        }
+    } else if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) {
+        return;
+    }
     const int ld = I.ld, Q = I.Q, Tc = I.Tc;
     double c[NTERMS];
     for (int j = 0; j < NTERMS; ++j) c[j] = 0.0;
@@ -523,7 +538,7 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
             if (role && (a & 1)) s = -s;
             if (valid) {
                 const size_t r = (size_t)(a * 2 * Q + role * Q + k) * ld + i;
-                if (I.tab32) I.tab32[r] = (float)s;
+                if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)s;
                 else I.tab[r] = s;
             }
         }
@@ -656,7 +671,7 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
             const double s = fma(Ay[((2 * a) * Qy + ky) * TILE + lane], z0, Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2);
             if (valid) {
                 const size_t r = (size_t)(8 * Q + a * Tc + t) * ld + i;
-                if (I.tab32) I.tab32[r] = (float)s;
+                if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)s;
                 else I.tab[r] = s;
             }
         }
@@ -672,13 +687,13 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
         }
         if (valid) {
             const size_t r = (size_t)(8 * Q + a * Tc + slot) * ld + i;
-            if (I.tab32) I.tab32[r] = (float)(sc[13 * TILE + lane] * s);
+            if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)(sc[13 * TILE + lane] * s);
             else I.tab[r] = sc[13 * TILE + lane] * s;
         }
     }
     if (wid == 0 && valid) {
         const size_t r = (size_t)(8 * Q + 4 * Tc) * ld + i;
-        if (I.tab32) I.tab32[r] = (float)sc[14 * TILE + lane];
+        if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)sc[14 * TILE + lane];
         else I.tab[r] = sc[14 * TILE + lane];
     }
 }
@@ -686,26 +701,53 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
 // ---------------------------------------------------------------------------
 // per-step residual and status
 // ---------------------------------------------------------------------------
+// Stagnation of a two-phase instance in its FP32 phase (window rule of FDLB_FP32_THEN_FP64).
+__device__ int stagnated(Inst& I, double r, double step) {
+    if (r == 0.0) return 1;
+    double* m = I.misc;
+    if (m[M_WIN_STEP] < 0.0) {
+        m[M_WIN_STEP] = step;
+        m[M_WIN_RESID] = r;
+        return 0;
+    }
+    if (step - m[M_WIN_STEP] < FDLB_STAGNATION_WINDOW) return 0;
+    if (!(r < FDLB_STAGNATION_FACTOR * m[M_WIN_RESID])) return 1;
+    m[M_WIN_STEP] = step;
+    m[M_WIN_RESID] = r;
+    return 0;
+}
+
 __global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double tol, double* resid_all) {
     Inst& I = insts[blockIdx.x];
     const int ld = I.ld, N = I.N;
     double* nd = I.node;
+    __shared__ double red[7][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (anchor >= -1) {
         if (anchor >= 0 && anchor != (int)blockIdx.x) return;
+        double m = 0.0;
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             nd[R_PREV_N * ld + i] = nd[R_N * ld + i];
             nd[R_PREV_UX * ld + i] = nd[R_UX * ld + i];
             nd[R_PREV_UY * ld + i] = nd[R_UY * ld + i];
             nd[R_PREV_T * ld + i] = nd[R_T * ld + i];
+            m = fma(I.dxw[i], nd[R_N * ld + i], m);
         }
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (lane == 0) red[0][wid] = m;
+        __syncthreads();
         if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[0][q];
+            I.misc[M_MASS0] = t;
             I.misc[M_RESID] = CUDART_INF;
+            I.misc[M_WIN_STEP] = -1.0;
             resid_all[blockIdx.x] = CUDART_INF;
         }
         return;
     }
     if (*I.status != FDLB_ACTIVE) return;
-    double s[6] = {0, 0, 0, 0, 0, 0};
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
     int bad_nf = 0, bad_ph = 0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const double n = nd[R_N * ld + i], ux = nd[R_UX * ld + i], uy = nd[R_UY * ld + i], T = nd[R_T * ld + i];
@@ -720,28 +762,28 @@ __global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double t
         s[3] += w * T * T;
         s[4] += w * dux * dux;
         s[5] += w * duy * duy;
+        s[6] += w * n;
         nd[R_PREV_N * ld + i] = n;
         nd[R_PREV_UX * ld + i] = ux;
         nd[R_PREV_UY * ld + i] = uy;
         nd[R_PREV_T * ld + i] = T;
     }
-    __shared__ double red[6][8];
-    __shared__ int flags[2];
-    if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; }
+    __shared__ int flags[3];
+    __shared__ double scale;
+    if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
     __syncthreads();
     if (bad_nf) atomicOr(&flags[0], 1);
     if (bad_ph) atomicOr(&flags[1], 1);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
+    for (int j = 0; j < 7; ++j) {
         double v = s[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[j][wid] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t[6];
-        for (int j = 0; j < 6; ++j) {
+        double t[7];
+        for (int j = 0; j < 7; ++j) {
             t[j] = 0.0;
             for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t[j] += red[j][q];
         }
@@ -749,9 +791,48 @@ __global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double t
         *I.steps += 1;
         I.misc[M_RESID] = r;
         resid_all[blockIdx.x] = r;
+        const bool fp32 = I.precision == FDLB_FP32_STORAGE;
         if (flags[0]) *I.status = FDLB_FAILED_NONFINITE;
         else if (flags[1]) *I.status = FDLB_FAILED_UNPHYSICAL;
+        else if (fp32 && r == 0.0 && I.two_phase) flags[2] = 1;   // FP32 f stopped changing
+        else if (fp32 && r == 0.0 && tol > 0.0) *I.status = FDLB_STAGNATED;
         else if (tol > 0.0 && r < tol) *I.status = FDLB_CONVERGED;
+        else if (I.two_phase && fp32) flags[2] = stagnated(I, r, (double)*I.steps);
+        scale = I.misc[M_MASS0] / t[6];
+    }
+    __syncthreads();
+    if (!flags[2]) return;
+    // Up-cast f: floats of F -> doubles in the stage buffer A, then back into F (which holds
+    // K ld doubles in a two-phase instance; A is free between steps), times the factor that
+    // restores the channel mass of the last anchor.  The discrete scheme conserves mass, but
+    // FP32 rounding near stagnation drops the same small updates step after step and lets the
+    // mass drift, which would move the FP64 steady state.  The node rows are rescaled alike
+    // (extensive rows by the factor, ln n and ln chi(eta0 n) anew; u and T are unchanged),
+    // so the next stage sees the moments of the rescaled f.
+    const double c = scale;
+    const size_t nf = (size_t)I.K * ld;
+    const float* src = static_cast<const float*>(I.f[0]);
+    double* tmp = static_cast<double*>(I.f[1]);
+    for (size_t e = threadIdx.x; e < nf; e += blockDim.x) tmp[e] = (double)src[e] * c;
+    __syncthreads();
+    double* dst = static_cast<double*>(I.f[0]);
+    for (size_t e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = tmp[e];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double n = nd[R_N * ld + i] * c;
+        nd[R_N * ld + i] = n;
+        nd[R_PREV_N * ld + i] *= c;
+        nd[R_QX * ld + i] *= c;
+        nd[R_QY * ld + i] *= c;
+        nd[R_PXX * ld + i] *= c;
+        nd[R_PXY * ld + i] *= c;
+        nd[R_SNEG * ld + i] *= c;
+        nd[R_SPOS * ld + i] *= c;
+        nd[R_LNN * ld + i] = log(n);
+        nd[R_LNCHI * ld + i] = log(chi_cs(I.eta0 * n));
+    }
+    if (threadIdx.x == 0) {
+        I.precision = FDLB_FP64;
+        I.misc[M_SWITCH] = (double)*I.steps;
     }
 }
 

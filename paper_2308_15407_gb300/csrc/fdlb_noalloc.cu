@@ -55,6 +55,10 @@ extern "C" int fdlb_step_noalloc(const fdlb_params* params, void* dev_f, size_t 
         fdlb::set_global_error("fdlb_step_noalloc: need params, dev_f and nsteps >= 0");
         return FDLB_EINVAL;
     }
+    if (params->precision == FDLB_FP32_THEN_FP64) {
+        fdlb::set_global_error("fdlb_step_noalloc: the two-phase precision form needs a context (fdlb_create)");
+        return FDLB_EINVAL;
+    }
     size_t need = fdlb_workspace_bytes(params, 1);
     if (need == 0) return FDLB_EINVAL;                     // message already set
     if (need > FDLB_NOALLOC_SCRATCH_BYTES) {

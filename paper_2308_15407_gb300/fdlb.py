@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(HERE, "libfdlb.so")
 FDLB_OK, FDLB_EINVAL, FDLB_ENOMEM, FDLB_ECUDA, FDLB_ENONFINITE, FDLB_EUNPHYSICAL, FDLB_ETIMEOUT, FDLB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 FOURIER, COUETTE, POISEUILLE = 0, 1, 2
 GRID_UNIFORM, GRID_TANH = 0, 1
-FP64, FP32_STORAGE = 0, 1
-ACTIVE, CONVERGED, FAILED_NONFINITE, FAILED_UNPHYSICAL = 0, 1, 2, 3
+FP64, FP32_STORAGE, FP32_THEN_FP64 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32_STORAGE, "fp32+fp64": FP32_THEN_FP64}
+ACTIVE, CONVERGED, FAILED_NONFINITE, FAILED_UNPHYSICAL, STAGNATED = 0, 1, 2, 3, 4
 MOMENT_ROWS = ("n", "ux", "uy", "T", "qx", "qy", "Pxx", "Pxy")
 
 
@@ -61,7 +62,7 @@ class Params:
         p.nx = int(self.nx)
         p.grid = {"uniform": GRID_UNIFORM, "tanh": GRID_TANH}[self.grid]
         p.qx_half, p.qy, p.qz = int(self.qx_half), int(self.qy), int(self.qz)
-        p.precision = {"fp64": FP64, "fp32": FP32_STORAGE}[self.precision]
+        p.precision = PRECISIONS[self.precision]
         p.j1_shear = int(bool(self.j1_shear))
         p.reserved = 0
         p.stretch, p.kn, p.eta0 = float(self.stretch), float(self.kn), float(self.eta0)
@@ -94,6 +95,7 @@ def load() -> C.CDLL:
         "fdlb_run": (C.c_int, [vp, C.c_double, C.c_int64, C.c_int64, C.c_double]),
         "fdlb_moments": (C.c_int, [vp, C.c_int32, dp]),
         "fdlb_status": (C.c_int, [vp, dp, ip, lp]),
+        "fdlb_precision": (C.c_int, [vp, ip, lp]),
         "fdlb_set_profiles": (C.c_int, [vp, C.c_int32, dp, dp, dp]),
         "fdlb_state_bytes": (C.c_size_t, [vp, C.c_int32]),
         "fdlb_get_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
@@ -232,6 +234,14 @@ class Solver:
         self._check(self.lib.fdlb_status(self.ctx, _dptr(r), s.ctypes.data_as(C.POINTER(C.c_int32)),
                                          st.ctypes.data_as(C.POINTER(C.c_int64))))
         return r, s, st
+
+    def precision_state(self):
+        """(storage precision in use per instance, step of the FP32 -> FP64 switch or -1)."""
+        pr = np.zeros(self.count, dtype=np.int32)
+        sw = np.zeros(self.count, dtype=np.int64)
+        self._check(self.lib.fdlb_precision(self.ctx, pr.ctypes.data_as(C.POINTER(C.c_int32)),
+                                            sw.ctypes.data_as(C.POINTER(C.c_int64))))
+        return pr, sw
 
     def set_profiles(self, inst: int, n, uy, T):
         n, uy, T = (np.ascontiguousarray(x, dtype=np.float64) for x in (n, uy, T))

@@ -38,7 +38,8 @@ def test_every_declared_symbol_is_exported(F):
 
 def test_abi_version_and_struct(F):
     lib = F.load()
-    assert lib.fdlb_abi_version() == 1
+    hdr = open(os.path.join(ROOT, "include", "fdlb.h")).read()
+    assert lib.fdlb_abi_version() == int(re.search(r"#define FDLB_ABI_VERSION (\d+)", hdr).group(1))
     assert ctypes.sizeof(F.CParams) == 4 * 10 + 8 * 11
 
 
@@ -56,6 +57,24 @@ def test_parameter_validation(F):
     lib = F.load()
     assert lib.fdlb_workspace_bytes((F.CParams * 1)(c), 1) == 0
     assert b"struct_size" in lib.fdlb_last_error(None)
+
+
+def test_two_phase_precision_workspace(F):
+    """FP32-then-FP64 instances hold f at its FP64 size; unknown precisions are rejected."""
+    base = dict(nx=64, qx_half=4, qy=4, qz=4, kn=0.1, eta0=0.1)
+    b64 = F.workspace_bytes([F.Params(**base, precision="fp64")])
+    b32 = F.workspace_bytes([F.Params(**base, precision="fp32")])
+    b2 = F.workspace_bytes([F.Params(**base, precision="fp32+fp64")])
+    assert b32 < b64 < b2
+    c = F.Params(**base).to_c()
+    c.precision = 3
+    lib = F.load()
+    assert lib.fdlb_workspace_bytes((F.CParams * 1)(c), 1) == 0
+    assert b"precision" in lib.fdlb_last_error(None)
+    c.precision = F.FP32_THEN_FP64
+    # rejected before any device access
+    assert lib.fdlb_step_noalloc((F.CParams * 1)(c), ctypes.c_void_p(256), 1 << 20, 1, None, None) == F.FDLB_EINVAL
+    assert b"two-phase" in lib.fdlb_last_error(None)
 
 
 @pytest.mark.parametrize("Q", [1, 2, 4, 6, 8, 12, 16])
