@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define FDLB_ABI_VERSION 2
+#define FDLB_ABI_VERSION 3
 
 /* Return codes. */
 #define FDLB_OK            0
@@ -177,6 +177,33 @@ int fdlb_precision(fdlb_ctx* ctx, int32_t* storage, int64_t* switch_step);
 size_t fdlb_state_bytes(const fdlb_ctx* ctx, int32_t inst);
 int fdlb_get_state(fdlb_ctx* ctx, int32_t inst, void* host, size_t bytes);
 int fdlb_set_state(fdlb_ctx* ctx, int32_t inst, const void* host, size_t bytes);
+
+/* Schedules of fdlb_step.  Both compute the same arithmetic in the same order (results are
+ * bitwise identical); they differ in how the work reaches the GPU.
+ *   TILED:    one kernel per phase of an RK stage over every instance of the batch (work
+ *             lists of 32-node tiles), replayed from a CUDA graph of 16 steps.  Fills the GPU
+ *             with large batches.
+ *   RESIDENT: one thread-block cluster per instance (up to 16 CTAs) runs whole steps in one
+ *             launch, the phases separated by cluster barriers; instances advance
+ *             independently and a converged instance's cluster exits.  Suits small batches
+ *             and long solves, where the tiled schedule is bound by launch gaps and by the
+ *             latency of each phase.
+ *   AUTO:     (default) the first fdlb_step call with at least FDLB_AUTOTUNE_STEPS steps
+ *             times both (its own steps, half each) and keeps the faster; shorter calls use
+ *             TILED until then.
+ * fdlb_profile's per-kernel timing always uses the tiled schedule. */
+#define FDLB_SCHED_AUTO      0
+#define FDLB_SCHED_TILED     1
+#define FDLB_SCHED_RESIDENT  2
+#define FDLB_AUTOTUNE_STEPS  96
+
+/* Request a schedule (FDLB_EINVAL for RESIDENT when the device cannot launch the cluster
+ * kernel for this batch). */
+int fdlb_set_schedule(fdlb_ctx* ctx, int32_t schedule);
+
+/* Schedule in use (FDLB_SCHED_AUTO while not chosen yet) and the CTAs per cluster of the
+ * resident schedule (0 when it is unavailable).  Either pointer may be NULL. */
+int fdlb_get_schedule(const fdlb_ctx* ctx, int32_t* schedule, int32_t* cluster_ctas);
 
 /* Optional per-kernel timing with CUDA events recorded on the context's stream around every
  * launch (off by default).  fdlb_profile(ctx, 1) clears the records and starts recording,

@@ -42,12 +42,18 @@ struct fdlb_ctx {
     Work* d_upd = nullptr;
     Work* d_nod = nullptr;
     int n_mom = 0, n_upd = 0, n_nod = 0, qmax = 1;
+    int* d_list = nullptr;            // count ints: instances in resident-cluster order
     int* d_status_all = nullptr;      // count ints (Inst::status points here)
     long long* d_steps_all = nullptr;
     double* d_resid_all = nullptr;    // count doubles (misc[M_RESID] copies)
     cudaStream_t stream = nullptr;
     size_t smem_upd_f64 = 0, smem_upd_f32 = 0;
     bool any_fp32 = false, any_fp64 = false;
+    int ntab_max = 0;
+    // schedule (FDLB_SCHED_*): requested, and the one in use once chosen (0 = not yet)
+    int sched_req = FDLB_SCHED_AUTO, sched = 0;
+    int cs = 0;                       // CTAs per cluster of the resident schedule (0: unavailable)
+    size_t res_smem = 0;
     std::string err;
     // CUDA graph of GRAPH_STEPS steps for one freeze tolerance (replayed by fdlb_step)
     cudaGraphExec_t graph = nullptr;
@@ -63,6 +69,8 @@ struct fdlb_ctx {
         if (graph) cudaGraphExecDestroy(graph);
     }
 };
+
+static void choose_cluster(fdlb_ctx* c);
 
 // Record a start/stop event pair around one launch of class `kind` when profiling is on.
 static cudaError_t prof_mark(fdlb_ctx* c, int kind) {
@@ -388,7 +396,8 @@ Layout layout_of(const fdlb_params& p, int groups) {
 
 size_t global_bytes(int count, int n_mom, int n_upd, int n_nod) {
     return al256(sizeof(Inst) * count) + al256(sizeof(Work) * n_mom) + al256(sizeof(Work) * n_upd) + al256(sizeof(Work) * n_nod) +
-           al256(sizeof(int) * count) + al256(sizeof(long long) * count) + al256(sizeof(double) * count);
+           al256(sizeof(int) * count) + al256(sizeof(long long) * count) + al256(sizeof(double) * count) +
+           al256(sizeof(int) * count);
 }
 
 // Velocities per update block: small batches split a tile's velocities into chunks of 32 to
@@ -464,6 +473,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     c->d_status_all = reinterpret_cast<int*>(take(sizeof(int) * count));
     c->d_steps_all = reinterpret_cast<long long*>(take(sizeof(long long) * count));
     c->d_resid_all = reinterpret_cast<double*>(take(sizeof(double) * count));
+    c->d_list = reinterpret_cast<int*>(take(sizeof(int) * count));
 
     std::vector<Work> wm, wu, wn;
     std::vector<std::pair<int*, size_t>> counters;
@@ -686,6 +696,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             for (int role = 0; role < 3; ++role) wn.push_back({ii, t * TILE, role, 0});
         }
         c->qmax = std::max(c->qmax, Q);
+        c->ntab_max = std::max(c->ntab_max, L.ntab);
         size_t sm = (size_t)L.ntab * TILE;
         if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, sm * 8), c->any_fp64 = true;
         if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, sm * 4), c->any_fp32 = true;
@@ -703,6 +714,15 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         if (rc) { int e = rc; g_err = c->err; delete c; return e; }
         so += r.second;
     }
+    // resident clusters take the largest instances (nodes x velocities) first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long)c->inst[a].N * c->inst[a].K > (long)c->inst[b].N * c->inst[b].K;
+    });
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_list, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s), "upload list");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "upload list");
+    if (rc) { int e = rc; g_err = c->err; delete c; return e; }
     rc = cuda_check(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s), "upload descriptors");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_mom, wm.data(), sizeof(Work) * n_mom, cudaMemcpyHostToDevice, s), "upload work");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_upd, wu.data(), sizeof(Work) * n_upd, cudaMemcpyHostToDevice, s), "upload work");
@@ -710,6 +730,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     for (auto& cn : counters)
         if (!rc) rc = cuda_check(c, cudaMemsetAsync(cn.first, 0, cn.second, s), "clear counters");
     if (!rc) rc = cuda_check(c, prepare_kernels(c->smem_upd_f64, c->smem_upd_f32, c->qmax), "kernel attributes");
+    if (!rc) choose_cluster(c);
     if (!rc) rc = cuda_check(c, launch_setup(c->d_inst, count, s), "setup kernel");
     if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, n_mom, 0, c->any_fp64, c->any_fp32, s), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, count, 1, 0.0, c->d_resid_all, s), "residual kernel");
@@ -731,6 +752,48 @@ extern "C" int fdlb_info(const fdlb_ctx* ctx, int32_t inst, int32_t* nx, int32_t
 }
 
 static const int GRAPH_STEPS = 16;
+static const int RESIDENT_CHUNK = 256;     // steps per resident launch
+
+// Cluster size of the resident schedule: the largest candidate (at most the largest
+// instance's 3 x tiles nodal items) whose clusters for the whole batch fit on the GPU at once;
+// failing that, the candidate with the most CTAs resident at once.  cs = 0: unavailable.
+static void choose_cluster(fdlb_ctx* c) {
+    int items = 1;
+    for (auto& I : c->inst) items = std::max(items, 3 * ((I.N + TILE - 1) / TILE));
+    int best = 0, best_ctas = 0;
+    size_t best_smem = 0;
+    for (int cs : {16, 8, 4, 2, 1}) {
+        if (cs > items && cs > 1) continue;
+        size_t smem = 0;
+        int n = 0;
+        if (prepare_resident(c->qmax, c->ntab_max, cs, &smem) != cudaSuccess ||
+            resident_max_clusters(c->qmax, smem, cs, &n) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (n < 1) continue;
+        if (n >= c->count) {
+            best = cs;
+            best_smem = smem;
+            break;
+        }
+        if (n * cs > best_ctas) {
+            best = cs;
+            best_ctas = n * cs;
+            best_smem = smem;
+        }
+    }
+    c->cs = best;
+    c->res_smem = best_smem;
+    // the kernel attribute must match the size used at launch
+    if (best) {
+        size_t smem;
+        if (prepare_resident(c->qmax, c->ntab_max, best, &smem) != cudaSuccess) {
+            cudaGetLastError();
+            c->cs = 0;
+        }
+    }
+}
 
 // Capture GRAPH_STEPS steps into an executable graph (kernels only; no host synchronisation
 // inside).  The legacy default stream cannot be captured: then steps are launched directly.
@@ -765,9 +828,7 @@ static bool ensure_graph(fdlb_ctx* c, double tol) {
     return true;
 }
 
-extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
-    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_step: null context");
-    if (nsteps < 0 || !(freeze_tol >= 0)) return fail(c, FDLB_EINVAL, "fdlb_step: nsteps >= 0 and freeze_tol >= 0 required");
+static int step_tiled(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
     if (!c->prof && nsteps >= GRAPH_STEPS && ensure_graph(c, freeze_tol)) {
         while (nsteps >= GRAPH_STEPS) {
             cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
@@ -779,6 +840,79 @@ extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
         cudaError_t e = step_once(c, freeze_tol);
         if (e != cudaSuccess) return cuda_check(c, e, "fdlb_step launch");
     }
+    return FDLB_OK;
+}
+
+static int step_resident(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
+    while (nsteps > 0) {
+        const int n = (int)std::min<int64_t>(nsteps, RESIDENT_CHUNK);
+        cudaError_t e = launch_resident(c->d_inst, c->d_list, c->count, c->cs, c->qmax, c->res_smem, n, freeze_tol,
+                                        c->d_resid_all, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "fdlb_step resident launch");
+        nsteps -= n;
+    }
+    return FDLB_OK;
+}
+
+// Times TUNE steps of each schedule (after 16 warm-up steps of each) and keeps the faster.
+static int autotune(fdlb_ctx* c, double freeze_tol) {
+    const int WARM = 16, TUNE = (FDLB_AUTOTUNE_STEPS - 2 * WARM) / 2;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int rc = FDLB_OK;
+    for (auto& e : ev)
+        if (!rc) rc = cuda_check(c, cudaEventCreate(&e), "autotune events");
+    if (!rc) rc = step_tiled(c, WARM, freeze_tol);
+    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[0], c->stream), "autotune events");
+    if (!rc) rc = step_tiled(c, TUNE, freeze_tol);
+    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[1], c->stream), "autotune events");
+    if (!rc) rc = step_resident(c, WARM, freeze_tol);
+    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[2], c->stream), "autotune events");
+    if (!rc) rc = step_resident(c, TUNE, freeze_tol);
+    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[3], c->stream), "autotune events");
+    float t_tiled = 0.0f, t_res = 0.0f;
+    if (!rc) rc = cuda_check(c, cudaEventSynchronize(ev[3]), "autotune synchronize");
+    if (!rc) rc = cuda_check(c, cudaEventElapsedTime(&t_tiled, ev[0], ev[1]), "autotune timing");
+    if (!rc) rc = cuda_check(c, cudaEventElapsedTime(&t_res, ev[2], ev[3]), "autotune timing");
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+    if (!rc) c->sched = t_res < t_tiled ? FDLB_SCHED_RESIDENT : FDLB_SCHED_TILED;
+    return rc;
+}
+
+extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_step: null context");
+    if (nsteps < 0 || !(freeze_tol >= 0)) return fail(c, FDLB_EINVAL, "fdlb_step: nsteps >= 0 and freeze_tol >= 0 required");
+    if (c->prof) return step_tiled(c, nsteps, freeze_tol);
+    if (c->sched == 0) {
+        if (c->sched_req != FDLB_SCHED_AUTO) {
+            c->sched = c->sched_req;
+        } else if (c->cs == 0) {
+            c->sched = FDLB_SCHED_TILED;
+        } else if (nsteps >= FDLB_AUTOTUNE_STEPS) {
+            int rc = autotune(c, freeze_tol);
+            if (rc) return rc;
+            nsteps -= FDLB_AUTOTUNE_STEPS;
+        }
+    }
+    if (c->sched == FDLB_SCHED_RESIDENT) return step_resident(c, nsteps, freeze_tol);
+    return step_tiled(c, nsteps, freeze_tol);
+}
+
+extern "C" int fdlb_set_schedule(fdlb_ctx* c, int32_t schedule) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_set_schedule: null context");
+    if (schedule != FDLB_SCHED_AUTO && schedule != FDLB_SCHED_TILED && schedule != FDLB_SCHED_RESIDENT)
+        return fail(c, FDLB_EINVAL, "fdlb_set_schedule: unknown schedule");
+    if (schedule == FDLB_SCHED_RESIDENT && c->cs == 0)
+        return fail(c, FDLB_EINVAL, "fdlb_set_schedule: the resident cluster kernel cannot be launched for this batch");
+    c->sched_req = schedule;
+    c->sched = schedule == FDLB_SCHED_AUTO ? 0 : schedule;
+    return FDLB_OK;
+}
+
+extern "C" int fdlb_get_schedule(const fdlb_ctx* c, int32_t* schedule, int32_t* cluster_ctas) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_get_schedule: null context");
+    if (schedule) *schedule = c->sched;
+    if (cluster_ctas) *cluster_ctas = c->cs;
     return FDLB_OK;
 }
 
@@ -925,8 +1059,11 @@ extern "C" int fdlb_get_state(fdlb_ctx* c, int32_t inst, void* host, size_t byte
         phase[0] = pr;
     }
     long long st = 0;
+    // in the FP32 phase only the first half of a two-phase f buffer is state; the rest is zeroed
+    const size_t fb = need - 24 - ph, used = (ph && phase[0] == FDLB_FP32_STORAGE) ? fb / 2 : fb;
+    if (used < fb) std::memset(static_cast<char*>(host) + 24 + ph + used, 0, fb - used);
     int rc = cuda_check(c, cudaMemcpyAsync(&st, I.steps, sizeof(st), cudaMemcpyDeviceToHost, c->stream), "state copy");
-    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(static_cast<char*>(host) + 24 + ph, I.f[0], need - 24 - ph, cudaMemcpyDeviceToHost, c->stream), "state copy");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(static_cast<char*>(host) + 24 + ph, I.f[0], used, cudaMemcpyDeviceToHost, c->stream), "state copy");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "state synchronize");
     if (rc) return rc;
     hdr[2] = (uint64_t)st;

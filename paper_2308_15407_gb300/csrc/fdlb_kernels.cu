@@ -22,6 +22,7 @@
 #include "fdlb_launch.h"
 #include "../../include/fdlb.h"
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -347,16 +348,16 @@ __device__ void finalize_moments(const Inst& I, int i, const double* s) {
     nd[R_LNCHI * ld + i] = log(chi_cs(I.eta0 * n));
 }
 
+// Named barrier over `n` threads (the moment items run on 128-thread halves of a block).
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// Raw sums of one (tile, x-velocity group) item by 128 threads (tid 0..127, barrier `bar`);
+// `part` holds MOM3_WARPS x MOM_SUMS x TILE doubles.  With one group the moments are written;
+// otherwise the group's partial sums go to msum.
 template <typename S>
-__global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
-    __shared__ double part[MOM3_WARPS][MOM_SUMS][TILE];
-    __shared__ int last;
-    const Work w = work[blockIdx.x];
-    const Inst& I = insts[w.inst];
-    if (*I.status != FDLB_ACTIVE) return;
-    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int i = w.i0 + lane, grp = w.k0, tile = w.k1;
+__device__ void moments_item(const Inst& I, int i0, int grp, int buf, double* part, int tid, int bar) {
+    const int lane = tid & 31, g = tid >> 5;
+    const int i = i0 + lane;
     const int ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
     const int kx0 = grp * 2 * Q / G, kx1 = (grp + 1) * 2 * Q / G;
     const bool valid = i < I.N;
@@ -395,39 +396,30 @@ __global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __res
         o[12] = fma(p, S4, o[12]);
         o[13] += S5;
     }
+    named_sync(bar, 128);                 // the previous item's readers of `part` are done
 #pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) part[g][j][lane] = o[j];
-    __syncthreads();
+    for (int j = 0; j < MOM_SUMS; ++j) part[(g * MOM_SUMS + j) * TILE + lane] = o[j];
+    named_sync(bar, 128);
+    if (g != 0 || !valid) return;
+    double s[MOM_SUMS];
+#pragma unroll
+    for (int j = 0; j < MOM_SUMS; ++j) {
+        double v = 0.0;
+        for (int q = 0; q < MOM3_WARPS; ++q) v += part[(q * MOM_SUMS + j) * TILE + lane];
+        s[j] = v;
+    }
     if (G == 1) {
-        if (g != 0 || !valid) return;
-        double s[MOM_SUMS];
-#pragma unroll
-        for (int j = 0; j < MOM_SUMS; ++j) {
-            double v = 0.0;
-            for (int q = 0; q < MOM3_WARPS; ++q) v += part[q][j][lane];
-            s[j] = v;
-        }
         finalize_moments(I, i, s);
         return;
     }
-    if (g == 0) {
-        double* dst = I.msum + (size_t)grp * MOM_SUMS * ld + i;
-        if (valid)
+    double* dst = I.msum + (size_t)grp * MOM_SUMS * ld + i;
 #pragma unroll
-            for (int j = 0; j < MOM_SUMS; ++j) {
-                double v = 0.0;
-                for (int q = 0; q < MOM3_WARPS; ++q) v += part[q][j][lane];
-                dst[(size_t)j * ld] = v;
-            }
-        __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(I.mcnt + tile, 1) == G - 1;
-    __syncthreads();
-    if (!last || g != 0) return;
-    __threadfence();
-    if (threadIdx.x == 0) I.mcnt[tile] = 0;
-    if (!valid) return;
+    for (int j = 0; j < MOM_SUMS; ++j) dst[(size_t)j * ld] = s[j];
+}
+
+// Moments of node i from the G group partials, added in group order.
+__device__ void moments_final(const Inst& I, int i) {
+    const int ld = I.ld, G = I.mgroups;
     double s[MOM_SUMS];
 #pragma unroll
     for (int j = 0; j < MOM_SUMS; ++j) s[j] = 0.0;
@@ -437,6 +429,33 @@ __global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __res
         for (int j = 0; j < MOM_SUMS; ++j) s[j] += __ldcg(src + (size_t)j * ld);
     }
     finalize_moments(I, i, s);
+}
+
+// One block per (instance, 32-node tile, group of x-velocities); its 4 warps split the
+// transverse index or the x-velocities.  With one group per tile (large batches) the block
+// converts the sums to moments itself.  With G > 1 groups (small batches, to occupy the GPU)
+// each block writes its partial sums; the last block of the tile to arrive (ticket from an
+// atomic counter) adds the G partials in group order -- the result does not depend on the
+// arrival order -- converts them and resets the ticket.
+template <typename S>
+__global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
+    __shared__ double part[MOM3_WARPS * MOM_SUMS * TILE];
+    __shared__ int last;
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
+    if (*I.status != FDLB_ACTIVE) return;
+    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    moments_item<S>(I, w.i0, w.k0, buf, part, threadIdx.x, 1);
+    if (I.mgroups == 1) return;
+    if (threadIdx.x < 32) __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(I.mcnt + w.k1, 1) == I.mgroups - 1;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    if (threadIdx.x == 0) I.mcnt[w.k1] = 0;
+    const int i = w.i0 + threadIdx.x;
+    if (i < I.N) moments_final(I, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,15 +472,13 @@ __host__ __device__ inline int nodal_smem_doubles(int qmax) {
     return r01 > r2 ? r01 : r2;
 }
 
+// One (tile, role) item by a block of NOD_WARPS warps; nsm holds nodal_smem_doubles(QB)
+// doubles; fp32: the instance stores f in FP32 (tables go to tab32).
 template <int QB>
-__global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restrict__ insts, const Work* __restrict__ work) {
-    extern __shared__ __align__(16) double nsm[];
-    const Work w = work[blockIdx.x];
-    const Inst& I = insts[w.inst];
-    if (*I.status != FDLB_ACTIVE) return;
+__device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp32) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int role = w.k0;
-    const int i = w.i0 + lane;
+    const int i = i0 + lane;
+    __syncthreads();                      // the previous item's readers of nsm are done
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc;
     const bool valid = i < N;
     const int ic = valid ? i : N - 1;           // padding lanes work on a real node, write nothing
@@ -538,7 +555,7 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
             if (role && (a & 1)) s = -s;
             if (valid) {
                 const size_t r = (size_t)(a * 2 * Q + role * Q + k) * ld + i;
-                if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)s;
+                if (fp32) I.tab32[r] = (float)s;
                 else I.tab[r] = s;
             }
         }
@@ -552,7 +569,7 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
     const double T = nd[R_T * ld + ic], sT = sqrt(T);
     const int Qy = I.Qy, Qz = I.Qz;
     if (wid == NOD_WARPS - 1) {
-        if (w.i0 == 0 && lane == 0) {
+        if (i0 == 0 && lane == 0) {
             // zero net mass flux through each wall (Sec. III B): the outgoing wall-face flux is
             // the quadratic reconstruction (11 f_1 - 7 f_2 + 2 f_3)/6 of outgoing populations.
             const double oL = (11.0 * nd[R_SNEG * ld + 0] - 7.0 * nd[R_SNEG * ld + 1] + 2.0 * nd[R_SNEG * ld + 2]) / 6.0;
@@ -671,7 +688,7 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
             const double s = fma(Ay[((2 * a) * Qy + ky) * TILE + lane], z0, Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2);
             if (valid) {
                 const size_t r = (size_t)(8 * Q + a * Tc + t) * ld + i;
-                if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)s;
+                if (fp32) I.tab32[r] = (float)s;
                 else I.tab[r] = s;
             }
         }
@@ -687,15 +704,24 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
         }
         if (valid) {
             const size_t r = (size_t)(8 * Q + a * Tc + slot) * ld + i;
-            if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)(sc[13 * TILE + lane] * s);
+            if (fp32) I.tab32[r] = (float)(sc[13 * TILE + lane] * s);
             else I.tab[r] = sc[13 * TILE + lane] * s;
         }
     }
     if (wid == 0 && valid) {
         const size_t r = (size_t)(8 * Q + 4 * Tc) * ld + i;
-        if (I.precision == FDLB_FP32_STORAGE) I.tab32[r] = (float)sc[14 * TILE + lane];
+        if (fp32) I.tab32[r] = (float)sc[14 * TILE + lane];
         else I.tab[r] = sc[14 * TILE + lane];
     }
+}
+
+template <int QB>
+__global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restrict__ insts, const Work* __restrict__ work) {
+    extern __shared__ __align__(16) double nsm[];
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
+    if (*I.status != FDLB_ACTIVE) return;
+    nodal_item<QB>(I, w.i0, w.k0, nsm, I.precision == FDLB_FP32_STORAGE);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,36 +743,13 @@ __device__ int stagnated(Inst& I, double r, double step) {
     return 0;
 }
 
-__global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double tol, double* resid_all) {
-    Inst& I = insts[blockIdx.x];
+// Residual, status and (two-phase) precision switch of instance I (batch index idx) after a
+// step, by a block of 256 threads.
+__device__ void resid_item(Inst& I, int idx, double tol, double* resid_all) {
     const int ld = I.ld, N = I.N;
     double* nd = I.node;
     __shared__ double red[7][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (anchor >= -1) {
-        if (anchor >= 0 && anchor != (int)blockIdx.x) return;
-        double m = 0.0;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            nd[R_PREV_N * ld + i] = nd[R_N * ld + i];
-            nd[R_PREV_UX * ld + i] = nd[R_UX * ld + i];
-            nd[R_PREV_UY * ld + i] = nd[R_UY * ld + i];
-            nd[R_PREV_T * ld + i] = nd[R_T * ld + i];
-            m = fma(I.dxw[i], nd[R_N * ld + i], m);
-        }
-        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-        if (lane == 0) red[0][wid] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[0][q];
-            I.misc[M_MASS0] = t;
-            I.misc[M_RESID] = CUDART_INF;
-            I.misc[M_WIN_STEP] = -1.0;
-            resid_all[blockIdx.x] = CUDART_INF;
-        }
-        return;
-    }
-    if (*I.status != FDLB_ACTIVE) return;
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
     int bad_nf = 0, bad_ph = 0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double t
         double r = fmax(fmax(sqrt(t[0] / t[1]), sqrt(t[2] / t[3])), fmax(sqrt(t[4]), sqrt(t[5])));
         *I.steps += 1;
         I.misc[M_RESID] = r;
-        resid_all[blockIdx.x] = r;
+        resid_all[idx] = r;
         const bool fp32 = I.precision == FDLB_FP32_STORAGE;
         if (flags[0]) *I.status = FDLB_FAILED_NONFINITE;
         else if (flags[1]) *I.status = FDLB_FAILED_UNPHYSICAL;
@@ -834,6 +837,40 @@ __global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double t
         I.precision = FDLB_FP64;
         I.misc[M_SWITCH] = (double)*I.steps;
     }
+}
+
+
+__global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double tol, double* resid_all) {
+    Inst& I = insts[blockIdx.x];
+    const int ld = I.ld, N = I.N;
+    double* nd = I.node;
+    __shared__ double red[7][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (anchor >= -1) {
+        if (anchor >= 0 && anchor != (int)blockIdx.x) return;
+        double m = 0.0;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            nd[R_PREV_N * ld + i] = nd[R_N * ld + i];
+            nd[R_PREV_UX * ld + i] = nd[R_UX * ld + i];
+            nd[R_PREV_UY * ld + i] = nd[R_UY * ld + i];
+            nd[R_PREV_T * ld + i] = nd[R_T * ld + i];
+            m = fma(I.dxw[i], nd[R_N * ld + i], m);
+        }
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (lane == 0) red[0][wid] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[0][q];
+            I.misc[M_MASS0] = t;
+            I.misc[M_RESID] = CUDART_INF;
+            I.misc[M_WIN_STEP] = -1.0;
+            resid_all[blockIdx.x] = CUDART_INF;
+        }
+        return;
+    }
+    if (*I.status != FDLB_ACTIVE) return;
+    resid_item(I, blockIdx.x, tol, resid_all);
 }
 
 // ---------------------------------------------------------------------------
@@ -931,16 +968,12 @@ struct Tabs<float> {
     __device__ static const float* Ky(const Inst& I) { return I.Ky32; }
 };
 
+// Velocities [k0, k1) of one tile for RK stage `stage`, by UPD_WARPS warps (lane, warp wy);
+// smem_raw holds the tile's table (ntab x TILE values of C).
 template <typename S, typename C>
-__global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restrict__ insts, const Work* __restrict__ work, int stage) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, unsigned char* smem_raw, int lane, int wy) {
     C* stab = reinterpret_cast<C*>(smem_raw);
-    const Work w = work[blockIdx.x];
-    const Inst& I = insts[w.inst];
-    if (*I.status != FDLB_ACTIVE) return;
-    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
-    const int lane = threadIdx.x, wy = threadIdx.y;
-    const int i = w.i0 + lane;
+    const int i = i0 + lane;
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, ntab = I.ntab;
     const bool valid = i < N;
     const C* tabc = Tabs<C>::tab(I);
@@ -948,6 +981,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     const C* gLc = Tabs<C>::gL(I);
     const C* gRc = Tabs<C>::gR(I);
     const C* Kyc = Tabs<C>::Ky(I);
+    __syncthreads();                      // the previous item's readers of the table are done
     for (int r = wy; r < ntab; r += UPD_WARPS) stab[r * TILE + lane] = valid ? tabc[(size_t)r * ld + i] : (C)0;
     __syncthreads();
     const S* src = static_cast<const S*>(I.f[stage - 1]);
@@ -963,7 +997,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     const int Tz = I.form == FORM_UNREDUCED ? I.Qz : 2;
     const C ay = (C)I.accel_y;
     const C sixth = (C)(1.0 / 6.0);
-    for (int k = w.k0 + wy; k < w.k1; k += UPD_WARPS) {
+    for (int k = k0 + wy; k < k1; k += UPD_WARPS) {
         const int kx = k / Tc, t = k - kx * Tc;
         const bool pos = kx < Q;
         const C p = pxc[kx];
@@ -1020,6 +1054,104 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
         C out = cb * (fi + dt * L);
         if (stage != 1) out += ca * (C)F[(size_t)k * ld + i];
         dst[(size_t)k * ld + i] = (S)out;
+    }
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restrict__ insts, const Work* __restrict__ work, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
+    if (*I.status != FDLB_ACTIVE) return;
+    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    update_item<S, C>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// resident schedule: one thread-block cluster per instance runs whole steps
+// ---------------------------------------------------------------------------
+// The phases of a step are the items of the tiled kernels (identical arithmetic), spread over
+// the cluster's CTAs and separated by cluster barriers instead of kernel boundaries.  Every
+// CTA of a cluster passes the same barriers: the trip counts depend only on the instance and
+// on values broadcast from rank 0's shared memory.  Clusters never wait on each other.
+namespace cg = cooperative_groups;
+
+constexpr int RES_THREADS = TILE * NOD_WARPS;    // 256 = UPD_WARPS warps = two moment halves
+
+__host__ __device__ inline size_t resident_smem_bytes(int qmax, int ntab_max) {
+    const size_t mom = (size_t)2 * MOM3_WARPS * MOM_SUMS * TILE * sizeof(double);
+    const size_t nod = (size_t)nodal_smem_doubles(qmax) * sizeof(double);
+    const size_t upd = (size_t)ntab_max * TILE * sizeof(double);
+    size_t m = mom > nod ? mom : nod;
+    return m > upd ? m : upd;
+}
+
+template <typename S>
+__device__ void res_moments(const Inst& I, int buf, int rank, int CS, unsigned char* sm, cg::cluster_group& cl) {
+    const int tiles = (I.N + TILE - 1) / TILE, G = I.mgroups;
+    const int half = threadIdx.x >> 7;
+    double* part = reinterpret_cast<double*>(sm) + half * (MOM3_WARPS * MOM_SUMS * TILE);
+    for (int it = 2 * rank + half; it < tiles * G; it += 2 * CS)
+        moments_item<S>(I, (it / G) * TILE, it % G, buf, part, threadIdx.x & 127, 1 + half);
+    cl.sync();
+    if (G > 1) {
+        for (int tl = rank; tl < tiles; tl += CS) {
+            const int i = tl * TILE + threadIdx.x;
+            if (threadIdx.x < TILE && i < I.N) moments_final(I, i);
+        }
+        cl.sync();
+    }
+}
+
+template <int QB, typename S>
+__device__ void res_step(Inst& I, int idx, double tol, double* resid_all, int rank, int CS, unsigned char* sm,
+                         cg::cluster_group& cl) {
+    const int tiles = (I.N + TILE - 1) / TILE, K = I.K;
+    // velocity chunks of the update items: about two items per CTA
+    int nch = (2 * CS + tiles - 1) / tiles;
+    nch = nch < 1 ? 1 : (nch > (K + UPD_WARPS - 1) / UPD_WARPS ? (K + UPD_WARPS - 1) / UPD_WARPS : nch);
+    const int KC = ((K + nch - 1) / nch + UPD_WARPS - 1) / UPD_WARPS * UPD_WARPS;
+    nch = (K + KC - 1) / KC;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    for (int stage = 1; stage <= 3; ++stage) {
+        if (stage > 1) res_moments<S>(I, stage - 1, rank, CS, sm, cl);
+        for (int it = rank; it < 3 * tiles; it += CS)
+            nodal_item<QB>(I, (it / 3) * TILE, it % 3, reinterpret_cast<double*>(sm), sizeof(S) == 4);
+        cl.sync();
+        for (int it = rank; it < tiles * nch; it += CS) {
+            const int tl = it / nch, c = it - tl * nch, k0 = c * KC;
+            update_item<S, S>(I, tl * TILE, k0, min(K, k0 + KC), stage, sm, lane, wy);
+        }
+        cl.sync();
+    }
+    res_moments<S>(I, 0, rank, CS, sm, cl);
+    if (rank == 0) resid_item(I, idx, tol, resid_all);
+}
+
+// Cluster c of the grid advances instance list[c] by up to nsteps steps (it stops early when
+// the instance leaves ACTIVE).
+template <int QB>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident(Inst* insts, const int* list, int nsteps, double tol, double* resid_all) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    __shared__ int bc[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int idx = list[blockIdx.x / CS];
+    Inst& I = insts[idx];
+    for (int s = 0; s < nsteps; ++s) {
+        if (rank == 0 && threadIdx.x == 0) {
+            bc[0] = *(volatile int*)I.status;
+            bc[1] = *(volatile int*)&I.precision;
+        }
+        cl.sync();
+        const int* b0 = cl.map_shared_rank(bc, 0);
+        const int st = b0[0], prec = b0[1];
+        if (st != FDLB_ACTIVE) {
+            cl.sync();                    // nobody reads rank 0's shared memory after it exits
+            break;
+        }
+        if (prec == FDLB_FP64) res_step<QB, double>(I, idx, tol, resid_all, rank, CS, rsm, cl);
+        else res_step<QB, float>(I, idx, tol, resid_all, rank, CS, rsm, cl);
     }
 }
 
@@ -1081,6 +1213,66 @@ cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax) {
         nodal_done = smem;
     }
     return set_smem(smem64, smem32);
+}
+
+// Attributes only ever grow, so that contexts created earlier keep launching.
+template <int QB>
+static cudaError_t resident_config(size_t smem, int cs) {
+    static size_t smem_done = 0;
+    static bool nonportable = false;
+    cudaError_t e = cudaSuccess;
+    if (smem > smem_done) {
+        e = cudaFuncSetAttribute(k_resident<QB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) smem_done = smem;
+    }
+    if (e == cudaSuccess && cs > 8 && !nonportable) {
+        e = cudaFuncSetAttribute(k_resident<QB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) nonportable = true;
+    }
+    return e;
+}
+
+cudaError_t prepare_resident(int qmax, int ntab_max, int cs, size_t* smem) {
+    *smem = resident_smem_bytes(qmax, ntab_max);
+    return qmax <= 8 ? resident_config<8>(*smem, cs) : resident_config<QMAX>(*smem, cs);
+}
+
+template <int QB>
+static cudaError_t max_clusters(size_t smem, int cs, int* n) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(RES_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(n, k_resident<QB>, &cfg);
+}
+
+cudaError_t resident_max_clusters(int qmax, size_t smem, int cs, int* n) {
+    return qmax <= 8 ? max_clusters<8>(smem, cs, n) : max_clusters<QMAX>(smem, cs, n);
+}
+
+cudaError_t launch_resident(Inst* d_inst, const int* d_list, int nclusters, int cs, int qmax, size_t smem, int nsteps,
+                            double freeze_tol, double* d_resid_all, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(nclusters * cs);
+    cfg.blockDim = dim3(RES_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (qmax <= 8) return cudaLaunchKernelEx(&cfg, k_resident<8>, d_inst, d_list, nsteps, freeze_tol, d_resid_all);
+    return cudaLaunchKernelEx(&cfg, k_resident<QMAX>, d_inst, d_list, nsteps, freeze_tol, d_resid_all);
 }
 
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,

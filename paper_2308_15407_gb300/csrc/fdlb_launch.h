@@ -27,6 +27,18 @@ cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int q
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
                           bool f64, bool f32, cudaStream_t s);
 
+// Resident schedule: attributes (shared memory, cluster size cs) of the cluster kernel for
+// the batch's largest half-range order and table; *smem receives its dynamic shared memory.
+cudaError_t prepare_resident(int qmax, int ntab_max, int cs, size_t* smem);
+
+// Clusters of cs CTAs that can be resident at once.
+cudaError_t resident_max_clusters(int qmax, size_t smem, int cs, int* n);
+
+// nclusters clusters of cs CTAs; cluster c advances instance d_list[c] by up to nsteps steps
+// (residual, status and freezing as fdlb_step).
+cudaError_t launch_resident(Inst* d_inst, const int* d_list, int nclusters, int cs, int qmax, size_t smem, int nsteps,
+                            double freeze_tol, double* d_resid_all, cudaStream_t s);
+
 // Shared-memory attributes of the kernels that need more than 48 KB (call outside any capture).
 cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax);
 

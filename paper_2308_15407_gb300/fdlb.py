@@ -19,6 +19,8 @@ FOURIER, COUETTE, POISEUILLE = 0, 1, 2
 GRID_UNIFORM, GRID_TANH = 0, 1
 FP64, FP32_STORAGE, FP32_THEN_FP64 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32_STORAGE, "fp32+fp64": FP32_THEN_FP64}
+SCHED_AUTO, SCHED_TILED, SCHED_RESIDENT = 0, 1, 2
+SCHEDULES = {"auto": SCHED_AUTO, "tiled": SCHED_TILED, "resident": SCHED_RESIDENT}
 ACTIVE, CONVERGED, FAILED_NONFINITE, FAILED_UNPHYSICAL, STAGNATED = 0, 1, 2, 3, 4
 MOMENT_ROWS = ("n", "ux", "uy", "T", "qx", "qy", "Pxx", "Pxy")
 
@@ -96,6 +98,8 @@ def load() -> C.CDLL:
         "fdlb_moments": (C.c_int, [vp, C.c_int32, dp]),
         "fdlb_status": (C.c_int, [vp, dp, ip, lp]),
         "fdlb_precision": (C.c_int, [vp, ip, lp]),
+        "fdlb_set_schedule": (C.c_int, [vp, C.c_int32]),
+        "fdlb_get_schedule": (C.c_int, [vp, ip, ip]),
         "fdlb_set_profiles": (C.c_int, [vp, C.c_int32, dp, dp, dp]),
         "fdlb_state_bytes": (C.c_size_t, [vp, C.c_int32]),
         "fdlb_get_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
@@ -234,6 +238,16 @@ class Solver:
         self._check(self.lib.fdlb_status(self.ctx, _dptr(r), s.ctypes.data_as(C.POINTER(C.c_int32)),
                                          st.ctypes.data_as(C.POINTER(C.c_int64))))
         return r, s, st
+
+    def set_schedule(self, schedule: str):
+        """'auto' (time both on the first long step call), 'tiled' or 'resident'."""
+        self._check(self.lib.fdlb_set_schedule(self.ctx, SCHEDULES[schedule]))
+
+    def schedule(self):
+        """(schedule in use: 'auto' while not chosen, 'tiled' or 'resident'; CTAs per cluster)."""
+        sc, cs = C.c_int32(), C.c_int32()
+        self._check(self.lib.fdlb_get_schedule(self.ctx, C.byref(sc), C.byref(cs)))
+        return {v: k for k, v in SCHEDULES.items()}[sc.value], cs.value
 
     def precision_state(self):
         """(storage precision in use per instance, step of the FP32 -> FP64 switch or -1)."""
