@@ -379,7 +379,13 @@ Layout layout_of(const fdlb_params& p, int groups) {
     auto add32 = [&](size_t n) { nd += al256(n * 4) / 8; };
     add(6 * L.Tc); add32(6 * L.Tc); add32(6 * L.Tc);
     const bool f32 = p.precision != FDLB_FP64;             // FP32 tables (FP32 and two-phase)
-    if (f32) { add32(2 * Q); add32(p.nx); add32(QYMAX * QYMAX); add32(L.K); add32(L.K); }
+    if (f32) {
+        add32(2 * Q); add32(p.nx); add32(QYMAX * QYMAX); add32(L.K); add32(L.K);
+        // float pairs: xq, xw, xq8, xw8, xa, xb, xib, xH, yq, yw, yH, zq, zw, zH, fsq, fisq
+        add32(2 * MX); add32(2 * MX); add32(2 * MX8); add32(2 * MX8); add32(2 * Q); add32(2 * (Q + 1));
+        add32(2 * (Q + 1)); add32(2 * Q * Q); add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QYMAX * QYMAX);
+        add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QZMAX * QZMAX); add32(2 * (QYMAX + 2)); add32(2 * (QYMAX + 2));
+    }
     L.tables = nd * 8;
     const size_t es = p.precision == FDLB_FP32_STORAGE ? 4 : 8;
     L.fbuf = al256((size_t)L.K * L.ld * es);
@@ -666,6 +672,35 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             I.gL32 = const_cast<float*>(g32);
             put32(&g32, L.K);
             I.gR32 = const_cast<float*>(g32);
+            // float-pair copies: hi = nearest float, lo = the float nearest to the remainder
+            auto pairs = [&](const float2** dst, const double* dev, size_t n) {
+                const float** d = reinterpret_cast<const float**>(dst);
+                float* h2 = put32(d, 2 * n);
+                const double* src = host_of(dev);
+                for (size_t k = 0; k < n; ++k) {
+                    const float hi = (float)src[k];
+                    h2[2 * k] = hi;
+                    h2[2 * k + 1] = (float)(src[k] - (double)hi);
+                }
+            };
+            pairs(&I.xq2, I.xq, MX);
+            pairs(&I.xw2, I.xw, MX);
+            pairs(&I.xq82, I.xq8, MX8);
+            pairs(&I.xw82, I.xw8, MX8);
+            pairs(&I.xa2, I.xa, Q);
+            pairs(&I.xb2, I.xb, Q + 1);
+            pairs(&I.xib2, I.xib, Q + 1);
+            pairs(&I.xH2, I.xH, (size_t)Q * Q);
+            pairs(&I.yq2, I.yq, MYMAX);
+            pairs(&I.yw2, I.yw, MYMAX);
+            pairs(&I.yH2, I.yH, QYMAX * QYMAX);
+            pairs(&I.zq2, I.zq, MYMAX);
+            pairs(&I.zw2, I.zw, MYMAX);
+            pairs(&I.zH2, I.zH, QZMAX * QZMAX);
+            pairs(&I.fsq2, I.fsq, QYMAX + 2);
+            pairs(&I.fisq2, I.fisq, QYMAX + 2);
+            const float h0 = (float)I.x_h0;
+            I.x_h02 = make_float2(h0, (float)(I.x_h0 - (double)h0));
         }
         if (pos * 8 != L.tables) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: table layout mismatch"); }
         regions.push_back({tab_off, L.tables});
@@ -733,7 +768,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     if (!rc) choose_cluster(c);
     if (!rc) rc = cuda_check(c, launch_setup(c->d_inst, count, s), "setup kernel");
     if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, n_mom, 0, c->any_fp64, c->any_fp32, s), "moments kernel");
-    if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, count, 1, 0.0, c->d_resid_all, s), "residual kernel");
+    if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, count, -1, 0.0, c->d_resid_all, s), "residual kernel");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "fdlb_create synchronize");
     if (rc) { int e = rc; g_err = c->err; delete c; return e; }
     *out = c;

@@ -3,6 +3,7 @@
 #pragma once
 #include <stdint.h>
 #include <stddef.h>
+#include <vector_types.h>
 
 namespace fdlb {
 
@@ -87,6 +88,25 @@ struct Inst {
     float* gL32;               // [K]
     float* gR32;               // [K]
     float* tab32;              // [ntab*ld]
+    // (hi, lo) float pairs of the projection tables for the double-float closure of FP32
+    // storage (null otherwise); same lengths as the FP64 tables
+    const float2* xq2;
+    const float2* xw2;
+    const float2* xq82;
+    const float2* xw82;
+    const float2* xa2;
+    const float2* xb2;
+    const float2* xib2;
+    const float2* xH2;
+    const float2* yq2;
+    const float2* yw2;
+    const float2* yH2;
+    const float2* zq2;
+    const float2* zw2;
+    const float2* zH2;
+    const float2* fsq2;
+    const float2* fisq2;
+    float2 x_h02;
     void* f[3];                // RK buffers F, A, B; each K*ld elements of the storage type
     double* node;              // [NROWS*ld]
     double* tab;               // [ntab*ld] projection table (see below)

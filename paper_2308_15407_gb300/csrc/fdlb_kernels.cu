@@ -307,53 +307,107 @@ struct InnerSum<float> {
         hi = t;
         lo += err + e;
     }
+    // adds another pair's value h + l (TwoSum on the heads)
+    __device__ __forceinline__ void add_pair(float h, float l) {
+        const float t = hi + h;
+        const float bb = t - hi;
+        const float err = (hi - (t - bb)) + (h - bb);
+        hi = t;
+        lo += err + l;
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 // Per node: the 14 raw sums over all velocities, factorised as sum_kx px^a (sum_t w_j(t) f).
-// One block per (instance, 32-node tile, group of x-velocities); its 4 warps split the
-// transverse index.  With one group per tile (large batches) the block converts the sums to
-// moments itself.  With G > 1 groups (small batches, to occupy the GPU) each block writes its
-// 14 partial sums; the last block of the tile to arrive (ticket from an atomic counter) adds
-// the G partials in group order -- the result does not depend on the arrival order -- converts
-// them and resets the ticket.
 constexpr int MOM3_WARPS = 4;
 
-__device__ void finalize_moments(const Inst& I, int i, const double* s) {
+// Temperature from the raw sums (the same operations wherever it is needed).
+__device__ __forceinline__ double sums_temperature(double n, double s1, double s2, double s3, double s4, double s6,
+                                                   double s7) {
+    const double ux = (s1 + s2) / n, uy = s3 / n;
+    const double Pxx = s4 - n * ux * ux, Pyy = s6 - n * uy * uy;
+    const double E = 0.5 * (Pxx + Pyy) + s7;
+    return E / (1.5 * n);
+}
+
+// Moments of the nodes of tile i0 from the raw sums ss[MOM_SUMS][TILE], by 128 threads: warp 0
+// writes the primitive rows, warps 1..3 ln n, ln T and ln chi(eta0 n) (independent FP64
+// chains on different schedulers).
+__device__ void finalize_tile(const Inst& I, int i0, const double* ss, int tid) {
+    const int lane = tid & 31, g = tid >> 5, i = i0 + lane;
+    if (i >= I.N) return;
     const int ld = I.ld;
-    const double n = s[0], sx = s[1] + s[2];
-    const double ux = sx / n, uy = s[3] / n;
-    const double Pxx = s[4] - n * ux * ux, Pxy = s[5] - n * ux * uy, Pyy = s[6] - n * uy * uy;
-    const double E = 0.5 * (Pxx + Pyy) + s[7];
-    const double T = E / (1.5 * n);
-    const double cx3 = s[8] - 3.0 * ux * s[4] + 2.0 * n * ux * ux * ux;
-    const double cxyy = s[9] - 2.0 * uy * s[5] - ux * s[6] + 2.0 * n * ux * uy * uy;
-    const double cxxy = s[10] - 2.0 * ux * s[5] - uy * s[4] + 2.0 * n * ux * ux * uy;
-    const double cy3 = s[11] - 3.0 * uy * s[6] + 2.0 * n * uy * uy * uy;
-    const double qx = 0.5 * (cx3 + cxyy) + (s[12] - ux * s[7]);
-    const double qy = 0.5 * (cy3 + cxxy) + (s[13] - uy * s[7]);
     double* nd = I.node;
-    nd[R_N * ld + i] = n;
-    nd[R_UX * ld + i] = ux;
-    nd[R_UY * ld + i] = uy;
-    nd[R_T * ld + i] = T;
-    nd[R_QX * ld + i] = qx;
-    nd[R_QY * ld + i] = qy;
-    nd[R_PXX * ld + i] = Pxx;
-    nd[R_PXY * ld + i] = Pxy;
-    nd[R_SNEG * ld + i] = s[1];
-    nd[R_SPOS * ld + i] = s[2];
-    nd[R_LNN * ld + i] = log(n);
-    nd[R_LNT * ld + i] = log(T);
-    nd[R_LNCHI * ld + i] = log(chi_cs(I.eta0 * n));
+    double s[MOM_SUMS];
+#pragma unroll
+    for (int j = 0; j < MOM_SUMS; ++j) s[j] = ss[j * TILE + lane];
+    const double n = s[0];
+    if (g == 1) {
+        nd[R_LNN * ld + i] = log(n);
+    } else if (g == 2) {
+        nd[R_LNT * ld + i] = log(sums_temperature(n, s[1], s[2], s[3], s[4], s[6], s[7]));
+    } else if (g == 3) {
+        nd[R_LNCHI * ld + i] = log(chi_cs(I.eta0 * n));
+    } else {
+        const double sx = s[1] + s[2];
+        const double ux = sx / n, uy = s[3] / n;
+        const double Pxx = s[4] - n * ux * ux, Pxy = s[5] - n * ux * uy;
+        const double T = sums_temperature(n, s[1], s[2], s[3], s[4], s[6], s[7]);
+        const double cx3 = s[8] - 3.0 * ux * s[4] + 2.0 * n * ux * ux * ux;
+        const double cxyy = s[9] - 2.0 * uy * s[5] - ux * s[6] + 2.0 * n * ux * uy * uy;
+        const double cxxy = s[10] - 2.0 * ux * s[5] - uy * s[4] + 2.0 * n * ux * ux * uy;
+        const double cy3 = s[11] - 3.0 * uy * s[6] + 2.0 * n * uy * uy * uy;
+        const double qx = 0.5 * (cx3 + cxyy) + (s[12] - ux * s[7]);
+        const double qy = 0.5 * (cy3 + cxxy) + (s[13] - uy * s[7]);
+        nd[R_N * ld + i] = n;
+        nd[R_UX * ld + i] = ux;
+        nd[R_UY * ld + i] = uy;
+        nd[R_T * ld + i] = T;
+        nd[R_QX * ld + i] = qx;
+        nd[R_QY * ld + i] = qy;
+        nd[R_PXX * ld + i] = Pxx;
+        nd[R_PXY * ld + i] = Pxy;
+        nd[R_SNEG * ld + i] = s[1];
+        nd[R_SPOS * ld + i] = s[2];
+    }
 }
 
 // Named barrier over `n` threads (the moment items run on 128-thread halves of a block).
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
+// Shared doubles of one moment item: MOM3_WARPS x MOM_SUMS x TILE warp partials + MOM_SUMS x
+// TILE sums.
+constexpr int MOM_SMEM = (MOM3_WARPS + 1) * MOM_SUMS * TILE;
+
+// Adds the x-velocity p's contribution to the 14 raw sums from the 6 transverse sums S.
+__device__ __forceinline__ void outer_sums(double* o, const double* S, double p, bool neg) {
+    const double p2 = p * p, p3 = p2 * p;
+    o[0] += S[0];
+    if (neg) o[1] = fma(p, S[0], o[1]); else o[2] = fma(p, S[0], o[2]);
+    o[3] += S[1];
+    o[4] = fma(p2, S[0], o[4]);
+    o[5] = fma(p, S[1], o[5]);
+    o[6] += S[2];
+    o[7] += S[4];
+    o[8] = fma(p3, S[0], o[8]);
+    o[9] = fma(p, S[2], o[9]);
+    o[10] = fma(p2, S[1], o[10]);
+    o[11] += S[3];
+    o[12] = fma(p, S[4], o[12]);
+    o[13] += S[5];
+}
+
+// Pair access for the FP32 cross-warp combination (no-ops for FP64 storage, never called).
+__device__ __forceinline__ float pair_hi(const InnerSum<float>& a) { return a.hi; }
+__device__ __forceinline__ float pair_lo(const InnerSum<float>& a) { return a.lo; }
+__device__ __forceinline__ void add_pair_to(InnerSum<float>& a, float h, float l) { a.add_pair(h, l); }
+__device__ __forceinline__ float pair_hi(const InnerSum<double>&) { return 0.0f; }
+__device__ __forceinline__ float pair_lo(const InnerSum<double>&) { return 0.0f; }
+__device__ __forceinline__ void add_pair_to(InnerSum<double>&, float, float) {}
+
 // Raw sums of one (tile, x-velocity group) item by 128 threads (tid 0..127, barrier `bar`);
-// `part` holds MOM3_WARPS x MOM_SUMS x TILE doubles.  With one group the moments are written;
-// otherwise the group's partial sums go to msum.
+// `part` holds MOM_SMEM doubles.  With one group the moments are written; otherwise the
+// group's partial sums go to msum.
 template <typename S>
 __device__ void moments_item(const Inst& I, int i0, int grp, int buf, double* part, int tid, int bar) {
     const int lane = tid & 31, g = tid >> 5;
@@ -369,6 +423,53 @@ __device__ void moments_item(const Inst& I, int i0, int grp, int buf, double* pa
     // warps own whole x-velocities when the block has at least as many as warps (the FP64 outer
     // sums then run once per x-velocity); otherwise they split the transverse index
     const bool by_kx = kx1 - kx0 >= MOM3_WARPS;
+    double* ss = part + MOM3_WARPS * MOM_SUMS * TILE;
+    if (sizeof(S) == 4 && !by_kx) {
+        // FP32 storage, warps split t: the warps' float pairs are combined in FP32 first, so the
+        // FP64 conversion and outer products run once per x-velocity (warp 0)
+        float* pb = reinterpret_cast<float*>(part);          // [MOM3_WARPS][NTW][2][TILE]
+        for (int kx = kx0; kx < kx1; ++kx) {
+            InnerSum<S> a[NTW];
+            const S* f = fb + (size_t)kx * Tc * ld;
+            for (int t = g; t < Tc; t += MOM3_WARPS) {
+                const S fv = valid ? f[(size_t)t * ld] : (S)0;
+#pragma unroll
+                for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], I.twh[j * Tc + t], I.twl[j * Tc + t]);
+            }
+            named_sync(bar, 128);         // the previous readers of `part` are done
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) {
+                pb[((g * NTW + j) * 2) * TILE + lane] = pair_hi(a[j]);
+                pb[((g * NTW + j) * 2 + 1) * TILE + lane] = pair_lo(a[j]);
+            }
+            named_sync(bar, 128);
+            if (g == 0) {
+                double Sv[NTW];
+#pragma unroll
+                for (int j = 0; j < NTW; ++j) {
+                    InnerSum<S> c = a[j];
+                    for (int q = 1; q < MOM3_WARPS; ++q)
+                        add_pair_to(c, pb[((q * NTW + j) * 2) * TILE + lane], pb[((q * NTW + j) * 2 + 1) * TILE + lane]);
+                    Sv[j] = c.value();
+                }
+                outer_sums(o, Sv, I.px[kx], kx >= Q);
+            }
+        }
+        if (g == 0) {
+            if (G > 1) {
+                if (valid)
+#pragma unroll
+                    for (int j = 0; j < MOM_SUMS; ++j) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = o[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < MOM_SUMS; ++j) ss[j * TILE + lane] = o[j];
+            }
+        }
+        if (G > 1) return;
+        named_sync(bar, 128);
+        finalize_tile(I, i0, ss, tid);
+        return;
+    }
     const int kxs = by_kx ? kx0 + g : kx0, kxstep = by_kx ? MOM3_WARPS : 1;
     const int t0 = by_kx ? 0 : g, tstep = by_kx ? 1 : MOM3_WARPS;
     for (int kx = kxs; kx < kx1; kx += kxstep) {
@@ -379,56 +480,44 @@ __device__ void moments_item(const Inst& I, int i0, int grp, int buf, double* pa
 #pragma unroll
             for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], I.twh[j * Tc + t], I.twl[j * Tc + t]);
         }
-        const double S0 = a[0].value(), S1 = a[1].value(), S2 = a[2].value(), S3 = a[3].value();
-        const double S4 = a[4].value(), S5 = a[5].value();
-        const double p = I.px[kx], p2 = p * p, p3 = p2 * p;
-        o[0] += S0;
-        if (kx >= Q) o[1] = fma(p, S0, o[1]); else o[2] = fma(p, S0, o[2]);
-        o[3] += S1;
-        o[4] = fma(p2, S0, o[4]);
-        o[5] = fma(p, S1, o[5]);
-        o[6] += S2;
-        o[7] += S4;
-        o[8] = fma(p3, S0, o[8]);
-        o[9] = fma(p, S2, o[9]);
-        o[10] = fma(p2, S1, o[10]);
-        o[11] += S3;
-        o[12] = fma(p, S4, o[12]);
-        o[13] += S5;
+        double Sv[NTW];
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) Sv[j] = a[j].value();
+        outer_sums(o, Sv, I.px[kx], kx >= Q);
     }
     named_sync(bar, 128);                 // the previous item's readers of `part` are done
 #pragma unroll
     for (int j = 0; j < MOM_SUMS; ++j) part[(g * MOM_SUMS + j) * TILE + lane] = o[j];
     named_sync(bar, 128);
-    if (g != 0 || !valid) return;
-    double s[MOM_SUMS];
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) {
+    // sums over the warps: warp g takes sums g, g + 4, ...
+    for (int j = g; j < MOM_SUMS; j += MOM3_WARPS) {
         double v = 0.0;
         for (int q = 0; q < MOM3_WARPS; ++q) v += part[(q * MOM_SUMS + j) * TILE + lane];
-        s[j] = v;
+        if (G > 1) {
+            if (valid) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = v;
+        } else {
+            ss[j * TILE + lane] = v;
+        }
     }
-    if (G == 1) {
-        finalize_moments(I, i, s);
-        return;
-    }
-    double* dst = I.msum + (size_t)grp * MOM_SUMS * ld + i;
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) dst[(size_t)j * ld] = s[j];
+    if (G > 1) return;
+    named_sync(bar, 128);
+    finalize_tile(I, i0, ss, tid);
 }
 
-// Moments of node i from the G group partials, added in group order.
-__device__ void moments_final(const Inst& I, int i) {
+// Moments of tile i0 from the G group partials, added in group order, by 128 threads.
+__device__ void moments_final_tile(const Inst& I, int i0, double* part, int tid, int bar) {
+    const int lane = tid & 31, g = tid >> 5, i = i0 + lane;
     const int ld = I.ld, G = I.mgroups;
-    double s[MOM_SUMS];
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) s[j] = 0.0;
-    for (int q = 0; q < G; ++q) {
-        const double* src = I.msum + (size_t)q * MOM_SUMS * ld + i;
-#pragma unroll
-        for (int j = 0; j < MOM_SUMS; ++j) s[j] += __ldcg(src + (size_t)j * ld);
+    double* ss = part + MOM3_WARPS * MOM_SUMS * TILE;
+    named_sync(bar, 128);                 // the previous item's readers of `ss` are done
+    for (int j = g; j < MOM_SUMS; j += MOM3_WARPS) {
+        double v = 0.0;
+        if (i < I.N)
+            for (int q = 0; q < G; ++q) v += __ldcg(I.msum + ((size_t)q * MOM_SUMS + j) * ld + i);
+        ss[j * TILE + lane] = v;
     }
-    finalize_moments(I, i, s);
+    named_sync(bar, 128);
+    finalize_tile(I, i0, ss, tid);
 }
 
 // One block per (instance, 32-node tile, group of x-velocities); its 4 warps split the
@@ -439,7 +528,7 @@ __device__ void moments_final(const Inst& I, int i) {
 // arrival order -- converts them and resets the ticket.
 template <typename S>
 __global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
-    __shared__ double part[MOM3_WARPS * MOM_SUMS * TILE];
+    __shared__ double part[MOM_SMEM];
     __shared__ int last;
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
@@ -447,15 +536,14 @@ __global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __res
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     moments_item<S>(I, w.i0, w.k0, buf, part, threadIdx.x, 1);
     if (I.mgroups == 1) return;
-    if (threadIdx.x < 32) __threadfence();
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(I.mcnt + w.k1, 1) == I.mgroups - 1;
     __syncthreads();
-    if (!last || threadIdx.x >= 32) return;
+    if (!last) return;
     __threadfence();
     if (threadIdx.x == 0) I.mcnt[w.k1] = 0;
-    const int i = w.i0 + threadIdx.x;
-    if (i < I.N) moments_final(I, i);
+    moments_final_tile(I, w.i0, part, threadIdx.x, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -466,10 +554,340 @@ __global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __res
 // role 2 = gradients, closure, coefficients, y and z projections and the transverse factors.
 // Shared doubles: role 0/1: [NOD_WARPS][4Q][32] partials + [4Q][32] sums;
 //                 role 2:   [20][32] scalars + Py [4 QYMAX][32] + Pz [3 QZMAX][32] + A [8 QYMAX][32].
+constexpr int CL_ROWS = 5 + 6 + 15;    // closure item: gradients, scalars, coefficients
+
 __host__ __device__ inline int nodal_smem_doubles(int qmax) {
     const int r01 = (NOD_WARPS + 1) * 4 * qmax * TILE;
-    const int r2 = (20 + 4 * QYMAX + 3 * QZMAX + 8 * QYMAX) * TILE;
+    const int r2 = (CL_ROWS + 4 * QYMAX + 3 * QZMAX + 8 * QYMAX) * TILE;
     return r01 > r2 ? r01 : r2;
+}
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic (unevaluated float pairs hi + lo, ~2^-46 relative) for the
+// projections of FP32-storage instances: their tables are rounded to FP32, and FP32 FMAs run
+// 64 times faster than FP64 FMAs on this GPU.  Error-free transformations (TwoSum, FMA
+// products, Dekker's fast two-sum) use the _rn intrinsics so that no contraction changes them.
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_fast(float a, float b) {      // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fadd_rn(b, __fsub_rn(a, s))};
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return df_fast(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast(p, e);
+}
+__device__ __forceinline__ df df_of(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ df df_of(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ float df_float(df a) { return __fadd_rn(a.hi, a.lo); }
+
+// 1/j as float pairs, j = 0..12 (set by prepare_kernels)
+__constant__ float2 c_inv2[13];
+
+// Half-range x projection of an FP32-storage tile (roles 0 / 1 of nodal_item) in double-float:
+// the same steps as the FP64 branch, with the per-node scalars sqrt(T), u and v computed once
+// in FP64 by warp 0 and shared.
+template <int QB>
+__device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = i0 + lane, N = I.N, ld = I.ld, Q = I.Q;
+    const bool valid = i < N;
+    const int ic = valid ? i : N - 1;
+    __shared__ float2 xs[4][TILE];                   // sqrt(T), u, v, v^2/2 as pairs
+    __shared__ int use_short;
+    if (wid == 0) {
+        const double T = I.node[R_T * ld + ic], ux = I.node[R_UX * ld + ic];
+        const double sT = sqrt(T), uu = role ? -ux : ux, v = uu / sT;
+        const df a = df_of(sT), b = df_of(uu), c = df_of(v), d = df_of(0.5 * v * v);
+        xs[0][lane] = make_float2(a.hi, a.lo);
+        xs[1][lane] = make_float2(b.hi, b.lo);
+        xs[2][lane] = make_float2(c.hi, c.lo);
+        xs[3][lane] = make_float2(d.hi, d.lo);
+        double av = valid ? fabs(v) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
+        if (lane == 0) use_short = av < 0.02 ? 1 : 2;
+    }
+    __syncthreads();
+    const bool short_rule = use_short == 1 && Q <= 12;
+    const int M = short_rule ? MX8 : MX;
+    const df sT = df_of(xs[0][lane]), uu = df_of(xs[1][lane]), v = df_of(xs[2][lane]), hv2 = df_of(xs[3][lane]);
+    df G[4][QB];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int l = 0; l < QB; ++l) G[a][l] = {0.0f, 0.0f};
+    const df one = {1.0f, 0.0f};
+    for (int m = wid; m < M; m += NOD_WARPS) {
+        const df q = df_of(short_rule ? I.xq82[m] : I.xq2[m]);
+        const df Wm = df_of(short_rule ? I.xw82[m] : I.xw2[m]);
+        const df z = q * v - hv2;
+        df ez;
+        if (short_rule) {
+            ez = one;
+#pragma unroll
+            for (int j = 12; j >= 1; --j) ez = ez * z * df_of(c_inv2[j]) + one;
+        } else {
+            ez = df_of(exp((double)z.hi + (double)z.lo));
+        }
+        const df x = sT * q, E = Wm * ez;
+        const df y = x - uu, e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+        df hm = {0.0f, 0.0f}, h = df_of(I.x_h02);
+#pragma unroll
+        for (int l = 0; l < QB; ++l) {
+            if (l < Q) {
+                G[0][l] = E * h + G[0][l];
+                G[1][l] = e1 * h + G[1][l];
+                G[2][l] = e2 * h + G[2][l];
+                G[3][l] = e3 * h + G[3][l];
+                const df hn = ((x - df_of(I.xa2[l])) * h - df_of(I.xb2[l]) * hm) * df_of(I.xib2[l + 1]);
+                hm = h;
+                h = hn;
+            }
+        }
+    }
+    float2* part = reinterpret_cast<float2*>(nsm);                  // [NOD_WARPS][4Q][32]
+    float2* sum = part + NOD_WARPS * 4 * Q * TILE;                  // [4Q][32]
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int l = 0; l < QB; ++l)
+            if (l < Q) part[((wid * 4 + a) * Q + l) * TILE + lane] = make_float2(G[a][l].hi, G[a][l].lo);
+    __syncthreads();
+    for (int r = wid; r < 4 * Q; r += NOD_WARPS) {
+        df t = {0.0f, 0.0f};
+        for (int q = 0; q < NOD_WARPS; ++q) t = t + df_of(part[(q * 4 * Q + r) * TILE + lane]);
+        sum[r * TILE + lane] = make_float2(t.hi, t.lo);
+    }
+    __syncthreads();
+    for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
+        const int a = o / Q, k = o - a * Q;
+        df t = {0.0f, 0.0f};
+        for (int l = 0; l < Q; ++l) t = df_of(I.xH2[l * Q + k]) * df_of(sum[(a * Q + l) * TILE + lane]) + t;
+        if (role && (a & 1)) t = -t;
+        if (valid) I.tab32[(size_t)(a * 2 * Q + role * Q + k) * ld + i] = df_float(t);
+    }
+}
+
+// Arithmetic of the closure item's projections: FP64 for FP64 storage, double-float for FP32
+// storage (whose tables are rounded to FP32).
+__device__ __forceinline__ double r_of(double x, double) { return x; }
+__device__ __forceinline__ df r_of(double x, df) { return df_of(x); }
+__device__ __forceinline__ double r_tab(const double* d, const float2*, int k, double) { return d[k]; }
+__device__ __forceinline__ df r_tab(const double*, const float2* p, int k, df) { return df_of(p[k]); }
+__device__ __forceinline__ double r_dbl(double x) { return x; }
+__device__ __forceinline__ double r_dbl(df x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ void r_store(const Inst& I, size_t r, double v) { I.tab[r] = v; }
+__device__ __forceinline__ void r_store(const Inst& I, size_t r, df v) { I.tab32[r] = df_float(v); }
+
+// Full-range projection row a of (p - u0)^a g on the Qn nodes (App. A): sum over the auxiliary
+// rule (M points) of w (p - u0)^a h_l(p), then the H matrix.  R: arithmetic type.
+template <typename R>
+__device__ void full_row(int a, int Qn, int M, const double* aq, const double* aw, const double* H, const float2* aq2,
+                         const float2* aw2, const float2* H2, const double* fsq, const double* fisq, const float2* fsq2,
+                         const float2* fisq2, R sT, R u0, R* P) {
+    const int lane = threadIdx.x & 31;
+    const R zero = r_of(0.0, R{}), one = r_of(1.0, R{});
+    R G[QYMAX > QZMAX ? QYMAX : QZMAX];
+#pragma unroll
+    for (int l = 0; l < QYMAX; ++l) G[l] = zero;
+    for (int m = 0; m < M; ++m) {
+        const R y = sT * r_tab(aq, aq2, m, R{}), x = u0 + y;
+        R e = r_tab(aw, aw2, m, R{});
+        for (int j = 0; j < a; ++j) e = e * y;
+        R hm = zero, h = one;
+#pragma unroll
+        for (int l = 0; l < QYMAX; ++l) {
+            if (l < Qn) {
+                G[l] = e * h + G[l];
+                const R hn = (x * h - r_tab(fsq, fsq2, l, R{}) * hm) * r_tab(fisq, fisq2, l + 1, R{});
+                hm = h;
+                h = hn;
+            }
+        }
+    }
+    for (int k2 = 0; k2 < Qn; ++k2) {
+        R t = zero;
+#pragma unroll
+        for (int l = 0; l < QYMAX; ++l)
+            if (l < Qn) t = r_tab(H, H2, l * Qn + k2, R{}) * G[l] + t;
+        P[k2 * TILE + lane] = t;
+    }
+}
+
+// Role 2 of a tile: gradients (Sec. III B 3), closure (Eqs. chi, prandtl, viscosity, tau), the
+// 13 coefficients of f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j) (Eq. j1), the y and z
+// projections (App. A) and the transverse factors n Y[a][t]; wall densities (Sec. III B).
+// Phase A: warps 0..4 one gradient each, warp 5 sqrt T, warp 6 the wall densities, warp 7 the
+// FP64 closure chain; phase B: coefficients and projection rows; phase C: assembly.
+template <typename R>
+__device__ void closure_item(const Inst& I, int i0, double* nsm) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = i0 + lane, N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, Qy = I.Qy, Qz = I.Qz;
+    const bool valid = i < N;
+    const int ic = valid ? i : N - 1;           // padding lanes work on a real node, write nothing
+    const double* nd = I.node;
+    double* gr = nsm;                           // [5][32] d/dx of ln n, ln chi, ln T, u_x, u_y
+    double* cs = gr + 5 * TILE;                 // [6][32] b rho chi, A, 1/T, mu0c X / (T n), sqrt T, n
+    R* sc = reinterpret_cast<R*>(cs + 6 * TILE);        // [15][32] coefficients, n, 1/tau
+    R* Py = sc + 15 * TILE;                             // [4 QYMAX][32]
+    R* Pz = Py + 4 * QYMAX * TILE;                      // [3 QZMAX][32]
+    R* Ay = Pz + 3 * QZMAX * TILE;                      // [8 QYMAX][32]
+    if (wid < 5) {
+        const int row = wid == 0 ? R_LNN : (wid == 1 ? R_LNCHI : (wid == 2 ? R_LNT : (wid == 3 ? R_UX : R_UY)));
+        const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
+        double g = 0.0;
+        for (int j = 0; j < 7; ++j) {
+            int idx;
+            double wj;
+            if (ic < 3) { idx = j; wj = I.gst[ic * 7 + j]; }
+            else if (ic > N - 4) { const int m = N - 1 - ic; idx = N - 1 - j; wj = -I.gst[m * 7 + j]; }
+            else { idx = ic - 3 + j; wj = cen[j]; }
+            g = fma(wj, nd[row * ld + idx], g);
+        }
+        gr[wid * TILE + lane] = g * I.xpinv[ic];
+    } else if (wid == 5) {
+        cs[4 * TILE + lane] = sqrt(nd[R_T * ld + ic]);
+    } else if (wid == 6) {
+        if (i0 == 0 && lane == 0) {
+            // zero net mass flux through each wall (Sec. III B): the outgoing wall-face flux is
+            // the quadratic reconstruction (11 f_1 - 7 f_2 + 2 f_3)/6 of outgoing populations.
+            const double oL = (11.0 * nd[R_SNEG * ld + 0] - 7.0 * nd[R_SNEG * ld + 1] + 2.0 * nd[R_SNEG * ld + 2]) / 6.0;
+            const double oR = (11.0 * nd[R_SPOS * ld + N - 1] - 7.0 * nd[R_SPOS * ld + N - 2] + 2.0 * nd[R_SPOS * ld + N - 3]) / 6.0;
+            I.misc[M_NWL] = -oL / I.misc[M_INL];
+            I.misc[M_NWR] = -oR / I.misc[M_INR];
+        }
+    } else {
+        const double k_mu = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
+        const double k_pd = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * CUDART_PI));
+        const double n = nd[R_N * ld + ic], T = nd[R_T * ld + ic];
+        const double eta = I.eta0 * n, chi = chi_cs(eta), br = 4.0 * eta, brc = br * chi;
+        const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_mu * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
+        const double iT = 1.0 / T, in = 1.0 / n;
+        cs[0 * TILE + lane] = brc;
+        cs[1 * TILE + lane] = (1.0 - Pr) * 0.2 * iT * iT * in;
+        cs[2 * TILE + lane] = iT;
+        cs[3 * TILE + lane] = I.mu0c * (1.0 / chi + 0.8 * br + k_mu * br * br * chi) * iT * in;
+        cs[5 * TILE + lane] = n;
+    }
+    __syncthreads();
+    {
+        // coefficients: tau = mu/(n T) = cs3 sqrt T, W = -tau b rho chi; warp w takes a few
+        const double tau = cs[3 * TILE + lane] * cs[4 * TILE + lane], W = -tau * cs[0 * TILE + lane];
+        const double A = cs[1 * TILE + lane], iT = cs[2 * TILE + lane];
+        const double Gr = 2.0 * gr[0 * TILE + lane] + gr[1 * TILE + lane] + gr[2 * TILE + lane];
+        const double Br = gr[2 * TILE + lane], Ur = gr[3 * TILE + lane], Vr = gr[4 * TILE + lane];
+        const double qx = nd[R_QX * ld + ic], qy = nd[R_QY * ld + ic];
+        const R z = r_of(0.0, R{});
+        switch (wid) {
+            case 0:
+                sc[0 * TILE + lane] = r_of(1.0 - W * Ur, z);
+                sc[13 * TILE + lane] = r_of(cs[5 * TILE + lane], z);
+                break;
+            case 1: sc[1 * TILE + lane] = r_of(-5.0 * A * qx + W * (Gr - 1.5 * Br), z); break;
+            case 2:
+                sc[2 * TILE + lane] = r_of(-5.0 * A * qy, z);
+                sc[6 * TILE + lane] = r_of(I.j1_shear ? W * 0.4 * Vr * iT : 0.0, z);
+                break;
+            case 3: {
+                const double u = W * Ur * iT;
+                sc[3 * TILE + lane] = r_of(0.6 * u, z);
+                sc[4 * TILE + lane] = r_of(0.2 * u, z);
+                sc[5 * TILE + lane] = sc[4 * TILE + lane];
+                break;
+            }
+            case 4: {
+                const R c3 = r_of(A * qx * iT + W * 0.3 * Br * iT, z);
+                sc[7 * TILE + lane] = c3;
+                sc[8 * TILE + lane] = c3;
+                sc[9 * TILE + lane] = c3;
+                break;
+            }
+            case 5: {
+                const R cy = r_of(A * qy * iT, z);
+                sc[10 * TILE + lane] = cy;
+                sc[11 * TILE + lane] = cy;
+                sc[12 * TILE + lane] = cy;
+                break;
+            }
+            case 6: sc[14 * TILE + lane] = r_of(1.0 / tau, z); break;
+            default: break;
+        }
+        // full-range projections: warps 0..3 rows a = wid of Py (p_y - u_y)^a g, warps 4..6 rows
+        // a = wid - 4 of Pz (p_z^a g)
+        if (I.form != FORM_REDUCED1D && (wid < 4 || (I.form == FORM_UNREDUCED && wid < 7))) {
+            const R sT = r_of(cs[4 * TILE + lane], z);
+            if (wid < 4)
+                full_row<R>(wid, Qy, I.My, I.yq, I.yw, I.yH, I.yq2, I.yw2, I.yH2, I.fsq, I.fisq, I.fsq2, I.fisq2, sT,
+                            r_of(nd[R_UY * ld + ic], z), Py + wid * QYMAX * TILE);
+            else
+                full_row<R>(wid - 4, Qz, I.Mz, I.zq, I.zw, I.zH, I.zq2, I.zw2, I.zH2, I.fsq, I.fisq, I.fsq2, I.fisq2, sT, z,
+                            Pz + (wid - 4) * QZMAX * TILE);
+        }
+    }
+    __syncthreads();
+    if (I.form != FORM_REDUCED1D) {
+        // A[a][c'][ky] = n sum over monomials (a, b, c = 2 c') of coef * Py[b][ky]
+        for (int o = wid; o < 8 * Qy; o += NOD_WARPS) {
+            const int ac = o / Qy, ky = o - ac * Qy, a = ac >> 1, c2 = ac & 1;
+            R t = r_of(0.0, R{});
+            for (int j = 0; j < NTERMS; ++j)
+                if (c_mono[j][0] == a && c_mono[j][2] == 2 * c2) t = sc[j * TILE + lane] * Py[(c_mono[j][1] * QYMAX + ky) * TILE + lane] + t;
+            Ay[o * TILE + lane] = sc[13 * TILE + lane] * t;
+        }
+        __syncthreads();
+        // transverse factors n Y[a][t] = A[a][0][ky] Z0(t) + A[a][1][ky] Z2(t)
+        const double T = nd[R_T * ld + ic];
+        const R Tr = r_of(T, R{}), one = r_of(1.0, R{}), T23 = r_of(3.0 * T * T, R{});
+        for (int o = wid; o < 4 * Tc; o += NOD_WARPS) {
+            const int a = o / Tc, t = o - a * Tc;
+            R z0, z2;
+            int ky;
+            if (I.form == FORM_UNREDUCED) {
+                ky = t / Qz;
+                const int kz = t - ky * Qz;
+                z0 = Pz[(0 * QZMAX + kz) * TILE + lane];
+                z2 = Pz[(2 * QZMAX + kz) * TILE + lane];
+            } else {
+                ky = t >> 1;
+                const bool theta = t & 1;
+                z0 = theta ? Tr : one;
+                z2 = theta ? T23 : Tr;
+            }
+            const R v = Ay[((2 * a) * Qy + ky) * TILE + lane] * z0 + Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2;
+            if (valid) r_store(I, (size_t)(8 * Q + a * Tc + t) * ld + i, v);
+        }
+    } else {
+        // 1D reduced (Sec. II B 1): slots phi, theta carry the (p_y, p_z) Gaussian moments
+        const int a = wid >> 1, slot = wid & 1;
+        const double T = nd[R_T * ld + ic];
+        double t = 0.0;
+        for (int j = 0; j < NTERMS; ++j) {
+            if (c_mono[j][0] != a) continue;
+            const int b = c_mono[j][1], cc = c_mono[j][2];
+            const double e = slot == 0 ? gmom(b, T) * gmom(cc, T) : gmom(b + 2, T) * gmom(cc, T) + gmom(b, T) * gmom(cc + 2, T);
+            t = fma(r_dbl(sc[j * TILE + lane]), e, t);
+        }
+        if (valid) r_store(I, (size_t)(8 * Q + a * Tc + slot) * ld + i, r_of(r_dbl(sc[13 * TILE + lane]) * t, R{}));
+    }
+    if (wid == 0 && valid) r_store(I, (size_t)(8 * Q + 4 * Tc) * ld + i, sc[14 * TILE + lane]);
 }
 
 // One (tile, role) item by a block of NOD_WARPS warps; nsm holds nodal_smem_doubles(QB)
@@ -479,6 +897,10 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = i0 + lane;
     __syncthreads();                      // the previous item's readers of nsm are done
+    if (fp32 && role < 2) {
+        xproj_df<QB>(I, i0, role, nsm);
+        return;
+    }
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc;
     const bool valid = i < N;
     const int ic = valid ? i : N - 1;           // padding lanes work on a real node, write nothing
@@ -488,17 +910,23 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
         // Q <= 12 the 8-point auxiliary rule is used (exact for v = 0 up to degree 15 >= Q + 2;
         // the neglected part of exp(q v) is below 1e-14 relative) with exp(q v - v^2/2) from its
         // Taylor series (|argument| < 0.12, 12 terms).  Warp w takes auxiliary points w, w + 8.
-        const double T = nd[R_T * ld + ic], ux = nd[R_UX * ld + ic];
-        const double sT = sqrt(T), uu = role ? -ux : ux, v = uu / sT;
-        // one rule per block so that the warps agree: the largest |v| of the tile decides
-        double av = valid ? fabs(v) : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
+        // sqrt T, u and v = u / sqrt T once per node (warp 0), shared; one rule per block so that
+        // the warps agree: the largest |v| of the tile decides
+        __shared__ double xs[3][TILE];
         __shared__ int use_short;
-        if (threadIdx.x == 0) use_short = 0;
+        if (wid == 0) {
+            const double T = nd[R_T * ld + ic], ux = nd[R_UX * ld + ic];
+            const double sT0 = sqrt(T), uu0 = role ? -ux : ux, v0 = uu0 / sT0;
+            xs[0][lane] = sT0;
+            xs[1][lane] = uu0;
+            xs[2][lane] = v0;
+            double av = valid ? fabs(v0) : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
+            if (lane == 0) use_short = av < 0.02 ? 1 : 2;
+        }
         __syncthreads();
-        if (lane == 0) atomicOr(&use_short, av < 0.02 ? 1 : 2);
-        __syncthreads();
+        const double sT = xs[0][lane], uu = xs[1][lane], v = xs[2][lane];
         const bool short_rule = use_short == 1 && Q <= 12;
         const int M = short_rule ? MX8 : MX;
         double G[4][QB];
@@ -561,158 +989,8 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
         }
         return;
     }
-    // ---------------- role 2
-    double* sc = nsm;                                              // [20][32]
-    double* Py = sc + 20 * TILE;                                   // [4 QYMAX][32]
-    double* Pz = Py + 4 * QYMAX * TILE;                            // [3 QZMAX][32]
-    double* Ay = Pz + 3 * QZMAX * TILE;                            // [8 QYMAX][32]
-    const double T = nd[R_T * ld + ic], sT = sqrt(T);
-    const int Qy = I.Qy, Qz = I.Qz;
-    if (wid == NOD_WARPS - 1) {
-        if (i0 == 0 && lane == 0) {
-            // zero net mass flux through each wall (Sec. III B): the outgoing wall-face flux is
-            // the quadratic reconstruction (11 f_1 - 7 f_2 + 2 f_3)/6 of outgoing populations.
-            const double oL = (11.0 * nd[R_SNEG * ld + 0] - 7.0 * nd[R_SNEG * ld + 1] + 2.0 * nd[R_SNEG * ld + 2]) / 6.0;
-            const double oR = (11.0 * nd[R_SPOS * ld + N - 1] - 7.0 * nd[R_SPOS * ld + N - 2] + 2.0 * nd[R_SPOS * ld + N - 3]) / 6.0;
-            I.misc[M_NWL] = -oL / I.misc[M_INL];
-            I.misc[M_NWR] = -oR / I.misc[M_INR];
-        }
-        // ---- gradients (Sec. III B 3), closure (Eqs. chi, prandtl, viscosity, tau) and the
-        // 13 coefficients of f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j) (Eq. j1)
-        const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
-        double gn = 0.0, gc = 0.0, gT = 0.0, gux = 0.0, guy = 0.0;
-        for (int j = 0; j < 7; ++j) {
-            int idx;
-            double wj;
-            if (ic < 3) { idx = j; wj = I.gst[ic * 7 + j]; }
-            else if (ic > N - 4) { const int m = N - 1 - ic; idx = N - 1 - j; wj = -I.gst[m * 7 + j]; }
-            else { idx = ic - 3 + j; wj = cen[j]; }
-            gn = fma(wj, nd[R_LNN * ld + idx], gn);
-            gc = fma(wj, nd[R_LNCHI * ld + idx], gc);
-            gT = fma(wj, nd[R_LNT * ld + idx], gT);
-            gux = fma(wj, nd[R_UX * ld + idx], gux);
-            guy = fma(wj, nd[R_UY * ld + idx], guy);
-        }
-        const double k_mu = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
-        const double k_pd = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * CUDART_PI));
-        const double xi = I.xpinv[ic];
-        const double Gr = (2.0 * gn + gc + gT) * xi, Br = gT * xi, Ur = gux * xi, Vr = guy * xi;
-        const double n = nd[R_N * ld + ic];
-        const double qx = nd[R_QX * ld + ic], qy = nd[R_QY * ld + ic];
-        const double eta = I.eta0 * n, chi = chi_cs(eta), br = 4.0 * eta, brc = br * chi;
-        const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_mu * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
-        const double iT = 1.0 / T;
-        const double mu = I.mu0c * sT * (1.0 / chi + 0.8 * br + k_mu * br * br * chi);
-        const double tau = mu * iT / n;
-        const double A = (1.0 - Pr) * 0.2 * iT * iT / n, W = -tau * brc;
-        sc[0 * TILE + lane] = 1.0 - W * Ur;
-        sc[1 * TILE + lane] = -5.0 * A * qx + W * (Gr - 1.5 * Br);
-        sc[2 * TILE + lane] = -5.0 * A * qy;
-        sc[3 * TILE + lane] = W * 0.6 * Ur * iT;
-        sc[4 * TILE + lane] = W * 0.2 * Ur * iT;
-        sc[5 * TILE + lane] = W * 0.2 * Ur * iT;
-        sc[6 * TILE + lane] = I.j1_shear ? W * 0.4 * Vr * iT : 0.0;
-        const double c3 = A * qx * iT + W * 0.3 * Br * iT, cy = A * qy * iT;
-        sc[7 * TILE + lane] = c3;
-        sc[8 * TILE + lane] = c3;
-        sc[9 * TILE + lane] = c3;
-        sc[10 * TILE + lane] = cy;
-        sc[11 * TILE + lane] = cy;
-        sc[12 * TILE + lane] = cy;
-        sc[13 * TILE + lane] = n;
-        sc[14 * TILE + lane] = 1.0 / tau;
-    } else if (I.form != FORM_REDUCED1D && (wid < 4 || I.form == FORM_UNREDUCED)) {
-        // ---- full-range projections (App. A): warps 0..3 row a = wid of Py (p_y - u_y)^a g,
-        // warps 4..6 row a = wid - 4 of Pz (p_z^a g); sum over the auxiliary rule in registers.
-        const bool ydir = wid < 4;
-        const int a = ydir ? wid : wid - 4;
-        const int Qn = ydir ? Qy : Qz, M = ydir ? I.My : I.Mz;
-        const double* aq = ydir ? I.yq : I.zq;
-        const double* aw = ydir ? I.yw : I.zw;
-        const double* H = ydir ? I.yH : I.zH;
-        const double u0 = ydir ? nd[R_UY * ld + ic] : 0.0;
-        double G[QYMAX > QZMAX ? QYMAX : QZMAX];
-#pragma unroll
-        for (int l = 0; l < QYMAX; ++l) G[l] = 0.0;
-        for (int m = 0; m < M; ++m) {
-            const double y = sT * aq[m], x = u0 + y;
-            double e = aw[m];
-            for (int j = 0; j < a; ++j) e *= y;
-            double hm = 0.0, h = 1.0;
-#pragma unroll
-            for (int l = 0; l < QYMAX; ++l) {
-                if (l < Qn) {
-                    G[l] = fma(e, h, G[l]);
-                    const double hn = (x * h - I.fsq[l] * hm) * I.fisq[l + 1];
-                    hm = h;
-                    h = hn;
-                }
-            }
-        }
-        double* P = ydir ? Py + a * QYMAX * TILE : Pz + a * QZMAX * TILE;
-        for (int k2 = 0; k2 < Qn; ++k2) {
-            double s = 0.0;
-#pragma unroll
-            for (int l = 0; l < QYMAX; ++l)
-                if (l < Qn) s = fma(H[l * Qn + k2], G[l], s);
-            P[k2 * TILE + lane] = s;
-        }
-    }
-    __syncthreads();
-    if (I.form != FORM_REDUCED1D) {
-        // A[a][c'][ky] = n sum over monomials (a, b, c = 2 c') of coef * Py[b][ky]
-        for (int o = wid; o < 8 * Qy; o += NOD_WARPS) {
-            const int ac = o / Qy, ky = o - ac * Qy, a = ac >> 1, c2 = ac & 1;
-            double s = 0.0;
-            for (int j = 0; j < NTERMS; ++j)
-                if (c_mono[j][0] == a && c_mono[j][2] == 2 * c2) s = fma(sc[j * TILE + lane], Py[(c_mono[j][1] * QYMAX + ky) * TILE + lane], s);
-            Ay[o * TILE + lane] = sc[13 * TILE + lane] * s;
-        }
-        __syncthreads();
-        // transverse factors n Y[a][t] = A[a][0][ky] Z0(t) + A[a][1][ky] Z2(t)
-        for (int o = wid; o < 4 * Tc; o += NOD_WARPS) {
-            const int a = o / Tc, t = o - a * Tc;
-            double z0, z2;
-            int ky;
-            if (I.form == FORM_UNREDUCED) {
-                ky = t / Qz;
-                const int kz = t - ky * Qz;
-                z0 = Pz[(0 * QZMAX + kz) * TILE + lane];
-                z2 = Pz[(2 * QZMAX + kz) * TILE + lane];
-            } else {
-                ky = t >> 1;
-                const bool theta = t & 1;
-                z0 = theta ? T : 1.0;
-                z2 = theta ? 3.0 * T * T : T;
-            }
-            const double s = fma(Ay[((2 * a) * Qy + ky) * TILE + lane], z0, Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2);
-            if (valid) {
-                const size_t r = (size_t)(8 * Q + a * Tc + t) * ld + i;
-                if (fp32) I.tab32[r] = (float)s;
-                else I.tab[r] = s;
-            }
-        }
-    } else if (wid < 8) {
-        // 1D reduced (Sec. II B 1): slots phi, theta carry the (p_y, p_z) Gaussian moments
-        const int a = wid >> 1, slot = wid & 1;
-        double s = 0.0;
-        for (int j = 0; j < NTERMS; ++j) {
-            if (c_mono[j][0] != a) continue;
-            const int b = c_mono[j][1], cc = c_mono[j][2];
-            const double e = slot == 0 ? gmom(b, T) * gmom(cc, T) : gmom(b + 2, T) * gmom(cc, T) + gmom(b, T) * gmom(cc + 2, T);
-            s = fma(sc[j * TILE + lane], e, s);
-        }
-        if (valid) {
-            const size_t r = (size_t)(8 * Q + a * Tc + slot) * ld + i;
-            if (fp32) I.tab32[r] = (float)(sc[13 * TILE + lane] * s);
-            else I.tab[r] = sc[13 * TILE + lane] * s;
-        }
-    }
-    if (wid == 0 && valid) {
-        const size_t r = (size_t)(8 * Q + 4 * Tc) * ld + i;
-        if (fp32) I.tab32[r] = (float)sc[14 * TILE + lane];
-        else I.tab[r] = sc[14 * TILE + lane];
-    }
+    if (fp32) closure_item<df>(I, i0, nsm);
+    else closure_item<double>(I, i0, nsm);
 }
 
 template <int QB>
@@ -1079,7 +1357,7 @@ namespace cg = cooperative_groups;
 constexpr int RES_THREADS = TILE * NOD_WARPS;    // 256 = UPD_WARPS warps = two moment halves
 
 __host__ __device__ inline size_t resident_smem_bytes(int qmax, int ntab_max) {
-    const size_t mom = (size_t)2 * MOM3_WARPS * MOM_SUMS * TILE * sizeof(double);
+    const size_t mom = (size_t)2 * MOM_SMEM * sizeof(double);
     const size_t nod = (size_t)nodal_smem_doubles(qmax) * sizeof(double);
     const size_t upd = (size_t)ntab_max * TILE * sizeof(double);
     size_t m = mom > nod ? mom : nod;
@@ -1090,15 +1368,13 @@ template <typename S>
 __device__ void res_moments(const Inst& I, int buf, int rank, int CS, unsigned char* sm, cg::cluster_group& cl) {
     const int tiles = (I.N + TILE - 1) / TILE, G = I.mgroups;
     const int half = threadIdx.x >> 7;
-    double* part = reinterpret_cast<double*>(sm) + half * (MOM3_WARPS * MOM_SUMS * TILE);
+    double* part = reinterpret_cast<double*>(sm) + half * MOM_SMEM;
     for (int it = 2 * rank + half; it < tiles * G; it += 2 * CS)
         moments_item<S>(I, (it / G) * TILE, it % G, buf, part, threadIdx.x & 127, 1 + half);
     cl.sync();
     if (G > 1) {
-        for (int tl = rank; tl < tiles; tl += CS) {
-            const int i = tl * TILE + threadIdx.x;
-            if (threadIdx.x < TILE && i < I.N) moments_final(I, i);
-        }
+        for (int tl = 2 * rank + half; tl < tiles; tl += 2 * CS)
+            moments_final_tile(I, tl * TILE, part, threadIdx.x & 127, 1 + half);
         cl.sync();
     }
 }
@@ -1204,6 +1480,19 @@ cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int q
 }
 
 cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax) {
+    static bool consts_done = false;
+    if (!consts_done) {
+        float2 h[13];
+        h[0] = make_float2(0.0f, 0.0f);
+        for (int j = 1; j < 13; ++j) {
+            const double v = 1.0 / j;
+            const float hi = (float)v;
+            h[j] = make_float2(hi, (float)(v - (double)hi));
+        }
+        cudaError_t e = cudaMemcpyToSymbol(c_inv2, h, sizeof(h));
+        if (e != cudaSuccess) return e;
+        consts_done = true;
+    }
     static int nodal_done = 0;
     const int smem = nodal_smem_doubles(qmax) * (int)sizeof(double);
     if (smem > 48 * 1024 && smem > nodal_done) {

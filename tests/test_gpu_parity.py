@@ -34,6 +34,18 @@ def test_heterogeneous_batch_fp64(steps):
     assert (st == F.ACTIVE).all() and (nst == steps).all()
 
 
+def test_first_step_residual_every_instance():
+    """Every instance of a batch is anchored at creation: its first residual is the oracle's."""
+    F = lib()
+    s = F.Solver([F.Params(**d) for d in HETERO])
+    s.step(1)
+    r, st, ns = s.status()
+    for i, d in enumerate(HETERO):
+        o = oracle_for(F.Params(**d))
+        o.step(1)
+        assert abs(r[i] / o.last_residual - 1.0) < 1e-8, (i, r[i], o.last_residual)
+
+
 def test_initial_state_matches_oracle():
     F = lib()
     ps = [F.Params(**kw) for kw in HETERO]

@@ -81,24 +81,24 @@ def test_switch_is_exact_upcast_then_fp64_parity():
 
 def test_two_phase_solve_below_fp32_floor():
     F = lib()
-    ps = [F.Params(**KW, precision=x) for x in ("fp32", "fp32+fp64", "fp64")]
+    ps = [F.Params(**KW, precision=x) for x in ("fp32+fp64", "fp32", "fp64")]
     s = F.Solver(ps)
     tol = 1e-11
     for _ in range(60):
         s.step(2000, tol)
         r, st, ns = s.status()
-        if st[1] != F.ACTIVE and st[2] != F.ACTIVE:
+        if st[0] != F.ACTIVE and st[2] != F.ACTIVE:
             break
     r, st, ns = s.status()
     pr, sw = s.precision_state()
     assert st[2] == F.CONVERGED and r[2] < tol
-    assert st[1] == F.CONVERGED and r[1] < tol, (r, st, ns)
-    assert pr[1] == F.FP64 and 0 < sw[1] < ns[1]
+    assert st[0] == F.CONVERGED and r[0] < tol, (r, st, ns)
+    assert pr[0] == F.FP64 and 0 < sw[0] < ns[0]
     # plain FP32 storage cannot resolve a residual this small
-    assert st[0] != F.CONVERGED, (r, st, ns)
+    assert st[1] != F.CONVERGED, (r, st, ns)
     # both FP64 endings describe the same steady state: the switch restored the mass that
     # FP32 rounding had moved
-    M1, M2 = s.moments(1), s.moments(2)
+    M1, M2 = s.moments(0), s.moments(2)
     for k in ("n", "T"):
         assert np.max(np.abs(M1[k] - M2[k]) / M2[k]) < 1e-7, k
     for k in ("ux", "qx"):
