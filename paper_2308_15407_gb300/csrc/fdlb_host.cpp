@@ -385,6 +385,7 @@ Layout layout_of(const fdlb_params& p, int groups) {
         add32(2 * MX); add32(2 * MX); add32(2 * MX8); add32(2 * MX8); add32(2 * Q); add32(2 * (Q + 1));
         add32(2 * (Q + 1)); add32(2 * Q * Q); add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QYMAX * QYMAX);
         add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QZMAX * QZMAX); add32(2 * (QYMAX + 2)); add32(2 * (QYMAX + 2));
+        add32(2 * 2 * Q);   // px pairs
     }
     L.tables = nd * 8;
     const size_t es = p.precision == FDLB_FP32_STORAGE ? 4 : 8;
@@ -699,6 +700,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             pairs(&I.zH2, I.zH, QZMAX * QZMAX);
             pairs(&I.fsq2, I.fsq, QYMAX + 2);
             pairs(&I.fisq2, I.fisq, QYMAX + 2);
+            pairs(&I.px2, I.px, 2 * Q);
             const float h0 = (float)I.x_h0;
             I.x_h02 = make_float2(h0, (float)(I.x_h0 - (double)h0));
         }

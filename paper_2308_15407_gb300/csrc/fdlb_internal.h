@@ -106,6 +106,7 @@ struct Inst {
     const float2* zH2;
     const float2* fsq2;
     const float2* fisq2;
+    const float2* px2;         // [2Q] x-velocities
     float2 x_h02;
     void* f[3];                // RK buffers F, A, B; each K*ld elements of the storage type
     double* node;              // [NROWS*ld]

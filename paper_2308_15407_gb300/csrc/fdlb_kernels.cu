@@ -279,6 +279,42 @@ __global__ void k_profiles(Inst* insts, int inst) {
 // ---------------------------------------------------------------------------
 // moments
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// double-float arithmetic (unevaluated float pairs hi + lo, ~2^-46 relative) for the
+// projections of FP32-storage instances: their tables are rounded to FP32, and FP32 FMAs run
+// 64 times faster than FP64 FMAs on this GPU.  Error-free transformations (TwoSum, FMA
+// products, Dekker's fast two-sum) use the _rn intrinsics so that no contraction changes them.
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_fast(float a, float b) {      // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fadd_rn(b, __fsub_rn(a, s))};
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return df_fast(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast(p, e);
+}
+__device__ __forceinline__ df df_of(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ df df_of(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ float df_float(df a) { return __fadd_rn(a.hi, a.lo); }
+
 constexpr int NTW = 6;     // transverse weights: mt, mt py, mt py^2, mt py^3, et, et py
 
 // Inner (transverse) running sum of w(t) f over t.  FP64 storage: an FP64 FMA.  FP32
@@ -397,13 +433,111 @@ __device__ __forceinline__ void outer_sums(double* o, const double* S, double p,
     o[13] += S[5];
 }
 
-// Pair access for the FP32 cross-warp combination (no-ops for FP64 storage, never called).
-__device__ __forceinline__ float pair_hi(const InnerSum<float>& a) { return a.hi; }
-__device__ __forceinline__ float pair_lo(const InnerSum<float>& a) { return a.lo; }
-__device__ __forceinline__ void add_pair_to(InnerSum<float>& a, float h, float l) { a.add_pair(h, l); }
-__device__ __forceinline__ float pair_hi(const InnerSum<double>&) { return 0.0f; }
-__device__ __forceinline__ float pair_lo(const InnerSum<double>&) { return 0.0f; }
-__device__ __forceinline__ void add_pair_to(InnerSum<double>&, float, float) {}
+
+// Outer sums in double-float (FP32 storage): as outer_sums, p and S as float pairs.
+__device__ __forceinline__ void outer_sums_df(df* o, const df* S, df p, bool neg) {
+    const df p2 = p * p, p3 = p2 * p;
+    o[0] = o[0] + S[0];
+    if (neg) o[1] = p * S[0] + o[1]; else o[2] = p * S[0] + o[2];
+    o[3] = o[3] + S[1];
+    o[4] = p2 * S[0] + o[4];
+    o[5] = p * S[1] + o[5];
+    o[6] = o[6] + S[2];
+    o[7] = o[7] + S[4];
+    o[8] = p3 * S[0] + o[8];
+    o[9] = p * S[2] + o[9];
+    o[10] = p2 * S[1] + o[10];
+    o[11] = o[11] + S[3];
+    o[12] = p * S[4] + o[12];
+    o[13] = o[13] + S[5];
+}
+
+// Normalised pair of an InnerSum<float> (TwoSum of head and tail).
+__device__ __forceinline__ df df_norm(float h, float l) {
+    const float s = __fadd_rn(h, l);
+    const float bb = __fsub_rn(s, h);
+    return {s, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(l, bb))};
+}
+
+// moments_item for FP32 storage: the transverse sums as float pairs, the outer sums over the
+// x-velocities and the sums over warps in double-float; FP64 only for the 14 final sums.
+__device__ void moments_item_f32(const Inst& I, int i0, int grp, int buf, double* part, int tid, int bar) {
+    const int lane = tid & 31, g = tid >> 5;
+    const int i = i0 + lane;
+    const int ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
+    const int kx0 = grp * 2 * Q / G, kx1 = (grp + 1) * 2 * Q / G;
+    const bool valid = i < I.N;
+    const float* fb = static_cast<const float*>(I.f[buf]) + (valid ? i : 0);
+    df o[MOM_SUMS];
+#pragma unroll
+    for (int j = 0; j < MOM_SUMS; ++j) o[j] = {0.0f, 0.0f};
+    const bool by_kx = kx1 - kx0 >= MOM3_WARPS;
+    float2* pb = reinterpret_cast<float2*>(part);            // [MOM3_WARPS][MOM_SUMS][TILE]
+    double* ss = part + MOM3_WARPS * MOM_SUMS * TILE;
+    if (by_kx) {
+        // warp g owns x-velocities kx0 + g, kx0 + g + 4, ...
+        for (int kx = kx0 + g; kx < kx1; kx += MOM3_WARPS) {
+            InnerSum<float> a[NTW];
+            const float* f = fb + (size_t)kx * Tc * ld;
+            for (int t = 0; t < Tc; ++t) {
+                const float fv = valid ? f[(size_t)t * ld] : 0.0f;
+#pragma unroll
+                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, I.twh[j * Tc + t], I.twl[j * Tc + t]);
+            }
+            df Sd[NTW];
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) Sd[j] = df_norm(a[j].hi, a[j].lo);
+            outer_sums_df(o, Sd, df_of(I.px2[kx]), kx >= Q);
+        }
+        named_sync(bar, 128);             // the previous item's readers of `part` are done
+    } else {
+        // the warps split t; their float pairs are combined in FP32 by warp 0
+        for (int kx = kx0; kx < kx1; ++kx) {
+            InnerSum<float> a[NTW];
+            const float* f = fb + (size_t)kx * Tc * ld;
+            for (int t = g; t < Tc; t += MOM3_WARPS) {
+                const float fv = valid ? f[(size_t)t * ld] : 0.0f;
+#pragma unroll
+                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, I.twh[j * Tc + t], I.twl[j * Tc + t]);
+            }
+            named_sync(bar, 128);         // the previous readers of `part` are done
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) pb[(g * MOM_SUMS + j) * TILE + lane] = make_float2(a[j].hi, a[j].lo);
+            named_sync(bar, 128);
+            if (g == 0) {
+                df Sd[NTW];
+#pragma unroll
+                for (int j = 0; j < NTW; ++j) {
+                    InnerSum<float> c = a[j];
+                    for (int q = 1; q < MOM3_WARPS; ++q) {
+                        const float2 v = pb[(q * MOM_SUMS + j) * TILE + lane];
+                        c.add_pair(v.x, v.y);
+                    }
+                    Sd[j] = df_norm(c.hi, c.lo);
+                }
+                outer_sums_df(o, Sd, df_of(I.px2[kx]), kx >= Q);
+            }
+        }
+        named_sync(bar, 128);
+    }
+#pragma unroll
+    for (int j = 0; j < MOM_SUMS; ++j) pb[(g * MOM_SUMS + j) * TILE + lane] = make_float2(o[j].hi, o[j].lo);
+    named_sync(bar, 128);
+    // sums over the warps in double-float: warp g takes sums g, g + 4, ...
+    for (int j = g; j < MOM_SUMS; j += MOM3_WARPS) {
+        df v = {0.0f, 0.0f};
+        for (int q = 0; q < MOM3_WARPS; ++q) v = v + df_of(pb[(q * MOM_SUMS + j) * TILE + lane]);
+        const double d = (double)v.hi + (double)v.lo;
+        if (G > 1) {
+            if (valid) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = d;
+        } else {
+            ss[j * TILE + lane] = d;
+        }
+    }
+    if (G > 1) return;
+    named_sync(bar, 128);
+    finalize_tile(I, i0, ss, tid);
+}
 
 // Raw sums of one (tile, x-velocity group) item by 128 threads (tid 0..127, barrier `bar`);
 // `part` holds MOM_SMEM doubles.  With one group the moments are written; otherwise the
@@ -424,50 +558,8 @@ __device__ void moments_item(const Inst& I, int i0, int grp, int buf, double* pa
     // sums then run once per x-velocity); otherwise they split the transverse index
     const bool by_kx = kx1 - kx0 >= MOM3_WARPS;
     double* ss = part + MOM3_WARPS * MOM_SUMS * TILE;
-    if (sizeof(S) == 4 && !by_kx) {
-        // FP32 storage, warps split t: the warps' float pairs are combined in FP32 first, so the
-        // FP64 conversion and outer products run once per x-velocity (warp 0)
-        float* pb = reinterpret_cast<float*>(part);          // [MOM3_WARPS][NTW][2][TILE]
-        for (int kx = kx0; kx < kx1; ++kx) {
-            InnerSum<S> a[NTW];
-            const S* f = fb + (size_t)kx * Tc * ld;
-            for (int t = g; t < Tc; t += MOM3_WARPS) {
-                const S fv = valid ? f[(size_t)t * ld] : (S)0;
-#pragma unroll
-                for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], I.twh[j * Tc + t], I.twl[j * Tc + t]);
-            }
-            named_sync(bar, 128);         // the previous readers of `part` are done
-#pragma unroll
-            for (int j = 0; j < NTW; ++j) {
-                pb[((g * NTW + j) * 2) * TILE + lane] = pair_hi(a[j]);
-                pb[((g * NTW + j) * 2 + 1) * TILE + lane] = pair_lo(a[j]);
-            }
-            named_sync(bar, 128);
-            if (g == 0) {
-                double Sv[NTW];
-#pragma unroll
-                for (int j = 0; j < NTW; ++j) {
-                    InnerSum<S> c = a[j];
-                    for (int q = 1; q < MOM3_WARPS; ++q)
-                        add_pair_to(c, pb[((q * NTW + j) * 2) * TILE + lane], pb[((q * NTW + j) * 2 + 1) * TILE + lane]);
-                    Sv[j] = c.value();
-                }
-                outer_sums(o, Sv, I.px[kx], kx >= Q);
-            }
-        }
-        if (g == 0) {
-            if (G > 1) {
-                if (valid)
-#pragma unroll
-                    for (int j = 0; j < MOM_SUMS; ++j) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = o[j];
-            } else {
-#pragma unroll
-                for (int j = 0; j < MOM_SUMS; ++j) ss[j * TILE + lane] = o[j];
-            }
-        }
-        if (G > 1) return;
-        named_sync(bar, 128);
-        finalize_tile(I, i0, ss, tid);
+    if (sizeof(S) == 4) {              // FP32 storage: double-float variant
+        moments_item_f32(I, i0, grp, buf, part, tid, bar);
         return;
     }
     const int kxs = by_kx ? kx0 + g : kx0, kxstep = by_kx ? MOM3_WARPS : 1;
@@ -562,44 +654,23 @@ __host__ __device__ inline int nodal_smem_doubles(int qmax) {
     return r01 > r2 ? r01 : r2;
 }
 
-// ---------------------------------------------------------------------------
-// double-float arithmetic (unevaluated float pairs hi + lo, ~2^-46 relative) for the
-// projections of FP32-storage instances: their tables are rounded to FP32, and FP32 FMAs run
-// 64 times faster than FP64 FMAs on this GPU.  Error-free transformations (TwoSum, FMA
-// products, Dekker's fast two-sum) use the _rn intrinsics so that no contraction changes them.
-// ---------------------------------------------------------------------------
-struct df {
-    float hi, lo;
-};
+// 1/j as float pairs, j = 0..16 (set by prepare_kernels)
+constexpr int NINV2 = 17;
+__constant__ float2 c_inv2[NINV2];
 
-__device__ __forceinline__ df df_fast(float a, float b) {      // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return {s, __fadd_rn(b, __fsub_rn(a, s))};
+// exp of a double-float: z = k ln 2 + r with |r| <= ln 2 / 2, e^r from its Taylor series to
+// r^14/14! (the rest is below 2^-57 relative), then the exact scaling by 2^k.  For |z| < 80.
+__device__ __forceinline__ df df_exp(df z) {
+    const df ln2 = {0.693147182464599609375f, -1.90465429995776787e-09f};
+    const float k = rintf(z.hi * 1.44269504088896341f);
+    const df r = z - ln2 * df{k, 0.0f};
+    const df one = {1.0f, 0.0f};
+    df e = one;
+#pragma unroll
+    for (int j = 14; j >= 1; --j) e = e * r * df_of(c_inv2[j]) + one;
+    const int ki = (int)k;
+    return {ldexpf(e.hi, ki), ldexpf(e.lo, ki)};
 }
-__device__ __forceinline__ df operator+(df a, df b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float bb = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-    return df_fast(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
-__device__ __forceinline__ df operator*(df a, df b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    return df_fast(p, e);
-}
-__device__ __forceinline__ df df_of(float2 v) { return {v.x, v.y}; }
-__device__ __forceinline__ df df_of(double x) {
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ float df_float(df a) { return __fadd_rn(a.hi, a.lo); }
-
-// 1/j as float pairs, j = 0..12 (set by prepare_kernels)
-__constant__ float2 c_inv2[13];
 
 // Half-range x projection of an FP32-storage tile (roles 0 / 1 of nodal_item) in double-float:
 // the same steps as the FP64 branch, with the per-node scalars sqrt(T), u and v computed once
@@ -645,7 +716,7 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
 #pragma unroll
             for (int j = 12; j >= 1; --j) ez = ez * z * df_of(c_inv2[j]) + one;
         } else {
-            ez = df_of(exp((double)z.hi + (double)z.lo));
+            ez = df_exp(z);
         }
         const df x = sT * q, E = Wm * ez;
         const df y = x - uu, e1 = E * y, e2 = e1 * y, e3 = e2 * y;
@@ -1482,9 +1553,9 @@ cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int q
 cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax) {
     static bool consts_done = false;
     if (!consts_done) {
-        float2 h[13];
+        float2 h[NINV2];
         h[0] = make_float2(0.0f, 0.0f);
-        for (int j = 1; j < 13; ++j) {
+        for (int j = 1; j < NINV2; ++j) {
             const double v = 1.0 / j;
             const float hi = (float)v;
             h[j] = make_float2(hi, (float)(v - (double)hi));
