@@ -333,9 +333,9 @@ def run_fdlb(args):
                 "kernel_ms_per_step": {k: v[0] / 2000 for k, v in prof.items()},
                 "measured_over": "2000 RK3 steps of the sweep after 600 start-up steps, per-launch CUDA events"}
     # launches in the timed region: per solve, 4 per instance for the reset (profiles x2,
-    # moments, residual anchor) and 10 per RK3 step of the batch until the last instance stops
-    # (fdlb_run advances in chunks of CHECK steps)
-    gpu_launches = sum(4 * s.count + 10 * CHECK * math.ceil(max(x) / CHECK) for x in steps_per_solve)
+    # moments, residual anchor) and 7 per RK3 step of the batch (closure and update per stage,
+    # residual) until the last instance stops (fdlb_run advances in chunks of CHECK steps)
+    gpu_launches = sum(4 * s.count + 7 * CHECK * math.ceil(max(x) / CHECK) for x in steps_per_solve)
 
     # ---- throughput regime: the 2048-instance mixed sweep in one batch (f ~0.6 GB > L2)
     batch = None

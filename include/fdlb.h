@@ -210,7 +210,8 @@ int fdlb_get_schedule(const fdlb_ctx* ctx, int32_t* schedule, int32_t* cluster_c
  * fdlb_profile(ctx, 0) stops.  fdlb_profile_read synchronises and returns, for kernel class
  * kind (0 moments, 1 per-node closure, 2 update, 3 residual), the summed duration in ms and
  * the number of launches recorded.  A launch of a class may run one kernel per storage
- * precision present in the batch. */
+ * precision present in the batch.  During steps the moments are computed in the epilogue of
+ * the update kernel (class 2); class 0 only records moments computed from scratch. */
 int fdlb_profile(fdlb_ctx* ctx, int32_t on);
 int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 

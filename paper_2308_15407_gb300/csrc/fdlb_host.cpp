@@ -38,10 +38,9 @@ struct fdlb_ctx {
     std::vector<fdlb_params> prm;
     std::vector<Inst> inst;           // host copies (device pointers inside)
     Inst* d_inst = nullptr;
-    Work* d_mom = nullptr;
     Work* d_upd = nullptr;
     Work* d_nod = nullptr;
-    int n_mom = 0, n_upd = 0, n_nod = 0, qmax = 1;
+    int n_upd = 0, n_nod = 0, qmax = 1;
     int* d_list = nullptr;            // count ints: instances in resident-cluster order
     int* d_status_all = nullptr;      // count ints (Inst::status points here)
     long long* d_steps_all = nullptr;
@@ -49,7 +48,7 @@ struct fdlb_ctx {
     cudaStream_t stream = nullptr;
     size_t smem_upd_f64 = 0, smem_upd_f32 = 0;
     bool any_fp32 = false, any_fp64 = false;
-    int ntab_max = 0;
+    int ntab_max = 0, ukc_max = 1;
     // schedule (FDLB_SCHED_*): requested, and the one in use once chosen (0 = not yet)
     int sched_req = FDLB_SCHED_AUTO, sched = 0;
     int cs = 0;                       // CTAs per cluster of the resident schedule (0: unavailable)
@@ -96,14 +95,12 @@ static cudaError_t step_once(fdlb_ctx* c, double freeze_tol) {
         if (e == cudaSuccess) e = fn();
         if (e == cudaSuccess) e = prof_mark(c, kind);
     };
+    // the update kernel's epilogue computes the moments of each stage's result
     for (int stage = 1; stage <= 3; ++stage) {
-        if (stage > 1)
-            guard(KK_MOMENTS, [&] { return launch_moments(c->d_inst, c->d_mom, c->n_mom, stage - 1, c->any_fp64, c->any_fp32, c->stream); });
         guard(KK_NODAL, [&] { return launch_nodal(c->d_inst, c->d_nod, c->n_nod, c->qmax, c->stream); });
         guard(KK_UPDATE, [&] { return launch_update(c->d_inst, c->d_upd, c->n_upd, stage, c->smem_upd_f64, c->smem_upd_f32,
                                                     c->any_fp64, c->any_fp32, c->stream); });
     }
-    guard(KK_MOMENTS, [&] { return launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream); });
     guard(KK_RESID, [&] { return launch_resid(c->d_inst, c->count, -2, freeze_tol, c->d_resid_all, c->stream); });
     return e;
 }
@@ -340,22 +337,22 @@ int validate(const fdlb_params& p, std::string& why) {
 // Byte layout of one instance inside the workspace.
 struct Layout {
     size_t tables = 0, fbuf = 0, node = 0, tab = 0, tab32 = 0, misc = 0, msum = 0, mcnt = 0, total = 0;
-    int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0, groups = 1;
+    int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0, groups = 1, ukc = 1;
 };
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Blocks per tile of the moment reduction: enough blocks to fill the GPU for small batches,
-// one block per tile (no partial buffer) for large ones.
-int mom_groups(const std::vector<fdlb_params>& ps) {
+// Velocities per update block: small batches split a tile's velocities into chunks of 32 to
+// occupy the GPU; large batches give a block the whole tile (the node table is loaded once),
+// at most 256 velocities (the block keeps its outputs in shared memory for the moments).
+constexpr int UKC_MAX = 256;
+int upd_chunk(const std::vector<fdlb_params>& ps) {
     long tiles = 0;
-    int qmax = 1;
-    for (auto& p : ps) { tiles += (p.nx + TILE - 1) / TILE; qmax = std::max(qmax, (int)p.qx_half); }
-    long g = (2048 + tiles - 1) / tiles;
-    return (int)std::max(1L, std::min<long>(g, 2 * qmax));
+    for (auto& p : ps) tiles += (p.nx + TILE - 1) / TILE;
+    return tiles >= 1216 ? UKC_MAX : 32;
 }
 
-Layout layout_of(const fdlb_params& p, int groups) {
+Layout layout_of(const fdlb_params& p, int ukc) {
     Layout L;
     L.form = p.qz > 0 ? FORM_UNREDUCED : (p.qy > 0 ? FORM_REDUCED2D : FORM_REDUCED1D);
     L.Tc = L.form == FORM_UNREDUCED ? p.qy * p.qz : (L.form == FORM_REDUCED2D ? 2 * p.qy : 2);
@@ -394,36 +391,27 @@ Layout layout_of(const fdlb_params& p, int groups) {
     L.tab = al256((size_t)L.ntab * L.ld * 8);
     L.misc = al256(8 * 8);
     L.tab32 = f32 ? al256((size_t)L.ntab * L.ld * 4) : 0;
-    L.groups = std::min(groups, 2 * p.qx_half);
+    L.ukc = std::min(L.K, ukc);
+    L.groups = (L.K + L.ukc - 1) / L.ukc;
     L.msum = L.groups > 1 ? al256((size_t)L.groups * MOM_SUMS * L.ld * 8) : 0;
     L.mcnt = al256((size_t)(L.ld / TILE) * 4);
     L.total = L.tables + 3 * L.fbuf + L.node + L.tab + L.tab32 + L.misc + L.msum + L.mcnt;
     return L;
 }
 
-size_t global_bytes(int count, int n_mom, int n_upd, int n_nod) {
-    return al256(sizeof(Inst) * count) + al256(sizeof(Work) * n_mom) + al256(sizeof(Work) * n_upd) + al256(sizeof(Work) * n_nod) +
+size_t global_bytes(int count, int n_upd, int n_nod) {
+    return al256(sizeof(Inst) * count) + al256(sizeof(Work) * n_upd) + al256(sizeof(Work) * n_nod) +
            al256(sizeof(int) * count) + al256(sizeof(long long) * count) + al256(sizeof(double) * count) +
            al256(sizeof(int) * count);
 }
 
-// Velocities per update block: small batches split a tile's velocities into chunks of 32 to
-// occupy the GPU; large batches give a block the whole tile (the node table is loaded once).
-int upd_chunk(const std::vector<fdlb_params>& ps) {
-    long tiles = 0;
-    for (auto& p : ps) tiles += (p.nx + TILE - 1) / TILE;
-    return tiles >= 1216 ? 1 << 20 : 32;
-}
-
-void count_work(const std::vector<fdlb_params>& p, int& n_mom, int& n_upd, int& n_nod) {
-    n_mom = n_upd = n_nod = 0;
-    const int G = mom_groups(p);
+void count_work(const std::vector<fdlb_params>& p, int& n_upd, int& n_nod) {
+    n_upd = n_nod = 0;
+    const int ukc = upd_chunk(p);
     for (auto& q : p) {
-        Layout L = layout_of(q, G);
+        Layout L = layout_of(q, ukc);
         int tiles = (q.nx + TILE - 1) / TILE;
-        n_mom += tiles * L.groups;
-        const int KC = std::min(L.K, upd_chunk(p));
-        n_upd += tiles * ((L.K + KC - 1) / KC);
+        n_upd += tiles * L.groups;
         n_nod += tiles * 3;
     }
 }
@@ -444,11 +432,11 @@ extern "C" size_t fdlb_workspace_bytes(const fdlb_params* params, int32_t count)
         std::string why;
         if (validate(p[i], why) != FDLB_OK) { g_err = "instance " + std::to_string(i) + ": " + why; return 0; }
     }
-    int n_mom, n_upd, n_nod;
-    count_work(p, n_mom, n_upd, n_nod);
-    size_t tot = global_bytes(count, n_mom, n_upd, n_nod);
-    const int G = mom_groups(p);
-    for (auto& q : p) tot += layout_of(q, G).total;
+    int n_upd, n_nod;
+    count_work(p, n_upd, n_nod);
+    size_t tot = global_bytes(count, n_upd, n_nod);
+    const int ukc = upd_chunk(p);
+    for (auto& q : p) tot += layout_of(q, ukc).total;
     return tot;
 }
 
@@ -465,16 +453,14 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     c->prm.assign(params, params + count);
     c->stream = reinterpret_cast<cudaStream_t>(stream);
 
-    int n_mom, n_upd, n_nod;
-    count_work(c->prm, n_mom, n_upd, n_nod);
-    c->n_mom = n_mom;
+    int n_upd, n_nod;
+    count_work(c->prm, n_upd, n_nod);
     c->n_upd = n_upd;
     c->n_nod = n_nod;
     char* base = reinterpret_cast<char*>(dev_workspace);
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base + off; off += al256(bytes); return p; };
     c->d_inst = reinterpret_cast<Inst*>(take(sizeof(Inst) * count));
-    c->d_mom = reinterpret_cast<Work*>(take(sizeof(Work) * n_mom));
     c->d_upd = reinterpret_cast<Work*>(take(sizeof(Work) * n_upd));
     c->d_nod = reinterpret_cast<Work*>(take(sizeof(Work) * n_nod));
     c->d_status_all = reinterpret_cast<int*>(take(sizeof(int) * count));
@@ -482,17 +468,16 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     c->d_resid_all = reinterpret_cast<double*>(take(sizeof(double) * count));
     c->d_list = reinterpret_cast<int*>(take(sizeof(int) * count));
 
-    std::vector<Work> wm, wu, wn;
+    std::vector<Work> wu, wn;
     std::vector<std::pair<int*, size_t>> counters;
     std::vector<char> staging;        // host image of all table regions
     std::vector<std::pair<size_t, size_t>> regions;   // (offset, size) of table regions
     size_t max_smem64 = 0, max_smem32 = 0;
 
-    const int mgroups = mom_groups(c->prm);
     const int ukc = upd_chunk(c->prm);
     for (int ii = 0; ii < count; ++ii) {
         const fdlb_params& p = c->prm[ii];
-        Layout L = layout_of(p, mgroups);
+        Layout L = layout_of(p, ukc);
         const int Q = p.qx_half, N = p.nx;
         Inst I;
         std::memset(&I, 0, sizeof(I));
@@ -500,7 +485,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         I.Mx = MX; I.My = L.My; I.Mz = L.Mz;
         I.precision = p.precision == FDLB_FP64 ? FDLB_FP64 : FDLB_FP32_STORAGE;
         I.two_phase = p.precision == FDLB_FP32_THEN_FP64;
-        I.j1_shear = p.j1_shear; I.ntab = L.ntab; I.mgroups = L.groups;
+        I.j1_shear = p.j1_shear; I.ntab = L.ntab; I.mgroups = L.groups; I.ukc = L.ukc;
         I.kn = p.kn; I.eta0 = p.eta0; I.chi0 = chi_cs(p.eta0);
         I.mu0c = (5.0 / 16.0) * std::sqrt(2.0 * M_PI) * I.chi0 * p.kn;
         I.accel_y = p.accel_y;
@@ -727,16 +712,14 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
 
         int tiles = (N + TILE - 1) / TILE;
         for (int t = 0; t < tiles; ++t) {
-            for (int g = 0; g < L.groups; ++g) wm.push_back({ii, t * TILE, g, t});
-            const int KC = std::min(L.K, ukc);
-            for (int k0 = 0; k0 < L.K; k0 += KC) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + KC)});
+            for (int k0 = 0; k0 < L.K; k0 += L.ukc) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + L.ukc)});
             for (int role = 0; role < 3; ++role) wn.push_back({ii, t * TILE, role, 0});
         }
         c->qmax = std::max(c->qmax, Q);
         c->ntab_max = std::max(c->ntab_max, L.ntab);
-        size_t sm = (size_t)L.ntab * TILE;
-        if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, sm * 8), c->any_fp64 = true;
-        if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, sm * 4), c->any_fp32 = true;
+        c->ukc_max = std::max(c->ukc_max, L.ukc);
+        if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, update_smem_bytes(L.ntab, L.ukc, 8, 8)), c->any_fp64 = true;
+        if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, update_smem_bytes(L.ntab, L.ukc, 4, 4)), c->any_fp32 = true;
     }
     if (off > need) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: workspace layout overflow"); }
     c->smem_upd_f64 = max_smem64;
@@ -761,7 +744,6 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "upload list");
     if (rc) { int e = rc; g_err = c->err; delete c; return e; }
     rc = cuda_check(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s), "upload descriptors");
-    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_mom, wm.data(), sizeof(Work) * n_mom, cudaMemcpyHostToDevice, s), "upload work");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_upd, wu.data(), sizeof(Work) * n_upd, cudaMemcpyHostToDevice, s), "upload work");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d_nod, wn.data(), sizeof(Work) * n_nod, cudaMemcpyHostToDevice, s), "upload work");
     for (auto& cn : counters)
@@ -769,7 +751,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     if (!rc) rc = cuda_check(c, prepare_kernels(c->smem_upd_f64, c->smem_upd_f32, c->qmax), "kernel attributes");
     if (!rc) choose_cluster(c);
     if (!rc) rc = cuda_check(c, launch_setup(c->d_inst, count, s), "setup kernel");
-    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, n_mom, 0, c->any_fp64, c->any_fp32, s), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_upd, n_upd, 0, c->ukc_max, c->any_fp64, c->any_fp32, s), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, count, -1, 0.0, c->d_resid_all, s), "residual kernel");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "fdlb_create synchronize");
     if (rc) { int e = rc; g_err = c->err; delete c; return e; }
@@ -803,7 +785,7 @@ static void choose_cluster(fdlb_ctx* c) {
         if (cs > items && cs > 1) continue;
         size_t smem = 0;
         int n = 0;
-        if (prepare_resident(c->qmax, c->ntab_max, cs, &smem) != cudaSuccess ||
+        if (prepare_resident(c->qmax, std::max(c->smem_upd_f64, c->smem_upd_f32), cs, &smem) != cudaSuccess ||
             resident_max_clusters(c->qmax, smem, cs, &n) != cudaSuccess) {
             cudaGetLastError();
             continue;
@@ -825,7 +807,7 @@ static void choose_cluster(fdlb_ctx* c) {
     // the kernel attribute must match the size used at launch
     if (best) {
         size_t smem;
-        if (prepare_resident(c->qmax, c->ntab_max, best, &smem) != cudaSuccess) {
+        if (prepare_resident(c->qmax, std::max(c->smem_upd_f64, c->smem_upd_f32), best, &smem) != cudaSuccess) {
             cudaGetLastError();
             c->cs = 0;
         }
@@ -1021,7 +1003,7 @@ extern "C" int fdlb_set_profiles(fdlb_ctx* c, int32_t inst, const double* n, con
     if (I.form == FORM_REDUCED1D) for (int i = 0; i < I.N; ++i) rows[2 * I.ld + i] = 0.0;
     int rc = cuda_check(c, cudaMemcpyAsync(I.node, rows.data(), sizeof(double) * rows.size(), cudaMemcpyHostToDevice, c->stream), "profiles upload");
     if (!rc) rc = cuda_check(c, launch_set_profiles(c->d_inst, inst, c->stream), "profiles kernel");
-    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_upd, c->n_upd, 0, c->ukc_max, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, c->count, inst, 0.0, c->d_resid_all, c->stream), "residual kernel");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "profiles synchronize");
     return rc;
@@ -1134,7 +1116,7 @@ extern "C" int fdlb_set_state(fdlb_ctx* c, int32_t inst, const void* host, size_
         if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.misc + M_SWITCH, &swd, sizeof(swd), cudaMemcpyHostToDevice, c->stream), "state upload");
     }
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.f[0], static_cast<const char*>(host) + 24 + ph, need - 24 - ph, cudaMemcpyHostToDevice, c->stream), "state upload");
-    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_upd, c->n_upd, 0, c->ukc_max, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, c->count, inst, 0.0, c->d_resid_all, c->stream), "residual kernel");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(I.steps, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream), "state upload");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "state synchronize");
@@ -1182,7 +1164,7 @@ int ctx_reanchor(fdlb_ctx* c, int inst) {
     static const int active = FDLB_ACTIVE;
     const Inst& I = c->inst[inst];
     int rc = cuda_check(c, cudaMemcpyAsync(I.status, &active, sizeof(int), cudaMemcpyHostToDevice, c->stream), "status reset");
-    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_mom, c->n_mom, 0, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
+    if (!rc) rc = cuda_check(c, launch_moments(c->d_inst, c->d_upd, c->n_upd, 0, c->ukc_max, c->any_fp64, c->any_fp32, c->stream), "moments kernel");
     if (!rc) rc = cuda_check(c, launch_resid(c->d_inst, c->count, inst, 0.0, c->d_resid_all, c->stream), "residual kernel");
     return rc;
 }

@@ -45,7 +45,8 @@ struct Inst {
     int j1_shear;
     int two_phase;             // FDLB_FP32_THEN_FP64: tables and buffers exist for both storages
     int ntab;                  // doubles per node in the projection table
-    int mgroups;               // x-velocity groups of the moment reduction (blocks per tile)
+    int ukc;                   // velocities per update block (chunk) of a tile
+    int mgroups;               // update chunks per tile (> 1: partial moment sums in msum)
     double kn, eta0, chi0, mu0c, dt, ds, accel_y;
     double T_L, T_R, U_L, U_R, T_init;
     double x_h0;               // h_0 of the half-range orthonormal family
@@ -113,7 +114,7 @@ struct Inst {
     double* tab;               // [ntab*ld] projection table (see below)
     double* misc;              // [NMISC]
     double* msum;              // [mgroups][14][ld] partial raw moment sums (mgroups > 1 only)
-    int* mcnt;                 // [tiles] arrival tickets of the moment CTAs of a tile (zero between uses)
+    int* mcnt;                 // [tiles] arrival tickets of the update chunks of a tile (zero between uses)
     int* status;
     long long* steps;
 };

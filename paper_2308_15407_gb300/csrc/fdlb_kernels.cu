@@ -408,12 +408,9 @@ __device__ void finalize_tile(const Inst& I, int i0, const double* ss, int tid) 
     }
 }
 
-// Named barrier over `n` threads (the moment items run on 128-thread halves of a block).
+// Named barrier over `n` threads (moment finalisation runs on 128-thread parts of a block).
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
-// Shared doubles of one moment item: MOM3_WARPS x MOM_SUMS x TILE warp partials + MOM_SUMS x
-// TILE sums.
-constexpr int MOM_SMEM = (MOM3_WARPS + 1) * MOM_SUMS * TILE;
 
 // Adds the x-velocity p's contribution to the 14 raw sums from the 6 transverse sums S.
 __device__ __forceinline__ void outer_sums(double* o, const double* S, double p, bool neg) {
@@ -459,148 +456,11 @@ __device__ __forceinline__ df df_norm(float h, float l) {
     return {s, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(l, bb))};
 }
 
-// moments_item for FP32 storage: the transverse sums as float pairs, the outer sums over the
-// x-velocities and the sums over warps in double-float; FP64 only for the 14 final sums.
-__device__ void moments_item_f32(const Inst& I, int i0, int grp, int buf, double* part, int tid, int bar) {
-    const int lane = tid & 31, g = tid >> 5;
-    const int i = i0 + lane;
-    const int ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
-    const int kx0 = grp * 2 * Q / G, kx1 = (grp + 1) * 2 * Q / G;
-    const bool valid = i < I.N;
-    const float* fb = static_cast<const float*>(I.f[buf]) + (valid ? i : 0);
-    df o[MOM_SUMS];
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) o[j] = {0.0f, 0.0f};
-    const bool by_kx = kx1 - kx0 >= MOM3_WARPS;
-    float2* pb = reinterpret_cast<float2*>(part);            // [MOM3_WARPS][MOM_SUMS][TILE]
-    double* ss = part + MOM3_WARPS * MOM_SUMS * TILE;
-    if (by_kx) {
-        // warp g owns x-velocities kx0 + g, kx0 + g + 4, ...
-        for (int kx = kx0 + g; kx < kx1; kx += MOM3_WARPS) {
-            InnerSum<float> a[NTW];
-            const float* f = fb + (size_t)kx * Tc * ld;
-            for (int t = 0; t < Tc; ++t) {
-                const float fv = valid ? f[(size_t)t * ld] : 0.0f;
-#pragma unroll
-                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, I.twh[j * Tc + t], I.twl[j * Tc + t]);
-            }
-            df Sd[NTW];
-#pragma unroll
-            for (int j = 0; j < NTW; ++j) Sd[j] = df_norm(a[j].hi, a[j].lo);
-            outer_sums_df(o, Sd, df_of(I.px2[kx]), kx >= Q);
-        }
-        named_sync(bar, 128);             // the previous item's readers of `part` are done
-    } else {
-        // the warps split t; their float pairs are combined in FP32 by warp 0
-        for (int kx = kx0; kx < kx1; ++kx) {
-            InnerSum<float> a[NTW];
-            const float* f = fb + (size_t)kx * Tc * ld;
-            for (int t = g; t < Tc; t += MOM3_WARPS) {
-                const float fv = valid ? f[(size_t)t * ld] : 0.0f;
-#pragma unroll
-                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, I.twh[j * Tc + t], I.twl[j * Tc + t]);
-            }
-            named_sync(bar, 128);         // the previous readers of `part` are done
-#pragma unroll
-            for (int j = 0; j < NTW; ++j) pb[(g * MOM_SUMS + j) * TILE + lane] = make_float2(a[j].hi, a[j].lo);
-            named_sync(bar, 128);
-            if (g == 0) {
-                df Sd[NTW];
-#pragma unroll
-                for (int j = 0; j < NTW; ++j) {
-                    InnerSum<float> c = a[j];
-                    for (int q = 1; q < MOM3_WARPS; ++q) {
-                        const float2 v = pb[(q * MOM_SUMS + j) * TILE + lane];
-                        c.add_pair(v.x, v.y);
-                    }
-                    Sd[j] = df_norm(c.hi, c.lo);
-                }
-                outer_sums_df(o, Sd, df_of(I.px2[kx]), kx >= Q);
-            }
-        }
-        named_sync(bar, 128);
-    }
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) pb[(g * MOM_SUMS + j) * TILE + lane] = make_float2(o[j].hi, o[j].lo);
-    named_sync(bar, 128);
-    // sums over the warps in double-float: warp g takes sums g, g + 4, ...
-    for (int j = g; j < MOM_SUMS; j += MOM3_WARPS) {
-        df v = {0.0f, 0.0f};
-        for (int q = 0; q < MOM3_WARPS; ++q) v = v + df_of(pb[(q * MOM_SUMS + j) * TILE + lane]);
-        const double d = (double)v.hi + (double)v.lo;
-        if (G > 1) {
-            if (valid) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = d;
-        } else {
-            ss[j * TILE + lane] = d;
-        }
-    }
-    if (G > 1) return;
-    named_sync(bar, 128);
-    finalize_tile(I, i0, ss, tid);
-}
-
-// Raw sums of one (tile, x-velocity group) item by 128 threads (tid 0..127, barrier `bar`);
-// `part` holds MOM_SMEM doubles.  With one group the moments are written; otherwise the
-// group's partial sums go to msum.
-template <typename S>
-__device__ void moments_item(const Inst& I, int i0, int grp, int buf, double* part, int tid, int bar) {
-    const int lane = tid & 31, g = tid >> 5;
-    const int i = i0 + lane;
-    const int ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
-    const int kx0 = grp * 2 * Q / G, kx1 = (grp + 1) * 2 * Q / G;
-    const bool valid = i < I.N;
-    const S* fb = static_cast<const S*>(I.f[buf]) + (valid ? i : 0);
-    // 0 n, 1 sneg, 2 spos, 3 sy, 4 sxx, 5 sxy, 6 syy, 7 se, 8 sxxx, 9 sxyy, 10 sxxy, 11 syyy, 12 sxe, 13 sye
-    double o[MOM_SUMS];
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) o[j] = 0.0;
-    // warps own whole x-velocities when the block has at least as many as warps (the FP64 outer
-    // sums then run once per x-velocity); otherwise they split the transverse index
-    const bool by_kx = kx1 - kx0 >= MOM3_WARPS;
-    double* ss = part + MOM3_WARPS * MOM_SUMS * TILE;
-    if (sizeof(S) == 4) {              // FP32 storage: double-float variant
-        moments_item_f32(I, i0, grp, buf, part, tid, bar);
-        return;
-    }
-    const int kxs = by_kx ? kx0 + g : kx0, kxstep = by_kx ? MOM3_WARPS : 1;
-    const int t0 = by_kx ? 0 : g, tstep = by_kx ? 1 : MOM3_WARPS;
-    for (int kx = kxs; kx < kx1; kx += kxstep) {
-        InnerSum<S> a[NTW];
-        const S* f = fb + (size_t)kx * Tc * ld;
-        for (int t = t0; t < Tc; t += tstep) {
-            const S fv = valid ? f[(size_t)t * ld] : (S)0;
-#pragma unroll
-            for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], I.twh[j * Tc + t], I.twl[j * Tc + t]);
-        }
-        double Sv[NTW];
-#pragma unroll
-        for (int j = 0; j < NTW; ++j) Sv[j] = a[j].value();
-        outer_sums(o, Sv, I.px[kx], kx >= Q);
-    }
-    named_sync(bar, 128);                 // the previous item's readers of `part` are done
-#pragma unroll
-    for (int j = 0; j < MOM_SUMS; ++j) part[(g * MOM_SUMS + j) * TILE + lane] = o[j];
-    named_sync(bar, 128);
-    // sums over the warps: warp g takes sums g, g + 4, ...
-    for (int j = g; j < MOM_SUMS; j += MOM3_WARPS) {
-        double v = 0.0;
-        for (int q = 0; q < MOM3_WARPS; ++q) v += part[(q * MOM_SUMS + j) * TILE + lane];
-        if (G > 1) {
-            if (valid) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = v;
-        } else {
-            ss[j * TILE + lane] = v;
-        }
-    }
-    if (G > 1) return;
-    named_sync(bar, 128);
-    finalize_tile(I, i0, ss, tid);
-}
-
-// Moments of tile i0 from the G group partials, added in group order, by 128 threads.
-__device__ void moments_final_tile(const Inst& I, int i0, double* part, int tid, int bar) {
+// Moments of tile i0 from the I.mgroups partials of its update chunks, added in chunk order,
+// by 128 threads (barrier `bar`); ss: MOM_SUMS x TILE doubles of shared memory.
+__device__ void moments_final_tile(const Inst& I, int i0, double* ss, int tid, int bar) {
     const int lane = tid & 31, g = tid >> 5, i = i0 + lane;
     const int ld = I.ld, G = I.mgroups;
-    double* ss = part + MOM3_WARPS * MOM_SUMS * TILE;
     named_sync(bar, 128);                 // the previous item's readers of `ss` are done
     for (int j = g; j < MOM_SUMS; j += MOM3_WARPS) {
         double v = 0.0;
@@ -610,32 +470,6 @@ __device__ void moments_final_tile(const Inst& I, int i0, double* part, int tid,
     }
     named_sync(bar, 128);
     finalize_tile(I, i0, ss, tid);
-}
-
-// One block per (instance, 32-node tile, group of x-velocities); its 4 warps split the
-// transverse index or the x-velocities.  With one group per tile (large batches) the block
-// converts the sums to moments itself.  With G > 1 groups (small batches, to occupy the GPU)
-// each block writes its partial sums; the last block of the tile to arrive (ticket from an
-// atomic counter) adds the G partials in group order -- the result does not depend on the
-// arrival order -- converts them and resets the ticket.
-template <typename S>
-__global__ void __launch_bounds__(TILE * MOM3_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
-    __shared__ double part[MOM_SMEM];
-    __shared__ int last;
-    const Work w = work[blockIdx.x];
-    const Inst& I = insts[w.inst];
-    if (*I.status != FDLB_ACTIVE) return;
-    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
-    moments_item<S>(I, w.i0, w.k0, buf, part, threadIdx.x, 1);
-    if (I.mgroups == 1) return;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(I.mcnt + w.k1, 1) == I.mgroups - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (threadIdx.x == 0) I.mcnt[w.k1] = 0;
-    moments_final_tile(I, w.i0, part, threadIdx.x, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1317,11 +1151,113 @@ struct Tabs<float> {
     __device__ static const float* Ky(const Inst& I) { return I.Ky32; }
 };
 
+// Shared memory of one update item: table, the chunk's outputs, per-warp moment sums, sums.
+__host__ __device__ inline size_t upd_table_bytes(int ntab, size_t c) { return ((size_t)ntab * TILE * c + 15) / 16 * 16; }
+__host__ __device__ inline size_t upd_smem_bytes(int ntab, int ukc, size_t c, size_t s) {
+    return upd_table_bytes(ntab, c) + (size_t)ukc * TILE * s + (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double);
+}
+
+// Epilogue of an update item: raw moment sums of the chunk's values fo[k - k0][lane] with the
+// factorisation of the moments (per x-velocity the transverse sums, then the outer sums over
+// x-velocities; FP32 pairs and double-float for FP32 storage), summed over the warps, then
+// the moments (one chunk per tile) or the chunk's partial sums in msum[grp].
+template <typename S>
+__device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, const S* fo, double* ex, int lane, int wy) {
+    const int i = i0 + lane, ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
+    const bool valid = i < I.N;
+    const int kxa = k0 / Tc, kxb = (k1 - 1) / Tc;
+    double* ss = ex + UPD_WARPS * MOM_SUMS * TILE;
+    if constexpr (sizeof(S) == 4) {
+        df o[MOM_SUMS];
+#pragma unroll
+        for (int j = 0; j < MOM_SUMS; ++j) o[j] = {0.0f, 0.0f};
+        for (int kx = kxa + wy; kx <= kxb; kx += UPD_WARPS) {
+            const int ta = max(0, k0 - kx * Tc), tb = min(Tc, k1 - kx * Tc);
+            InnerSum<float> a[NTW];
+            for (int t = ta; t < tb; ++t) {
+                const float fv = fo[(kx * Tc + t - k0) * TILE + lane];
+#pragma unroll
+                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, I.twh[j * Tc + t], I.twl[j * Tc + t]);
+            }
+            df Sd[NTW];
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) Sd[j] = df_norm(a[j].hi, a[j].lo);
+            outer_sums_df(o, Sd, df_of(I.px2[kx]), kx >= Q);
+        }
+        float2* pe = reinterpret_cast<float2*>(ex);
+#pragma unroll
+        for (int j = 0; j < MOM_SUMS; ++j) pe[(wy * MOM_SUMS + j) * TILE + lane] = make_float2(o[j].hi, o[j].lo);
+        __syncthreads();
+        for (int j = wy; j < MOM_SUMS; j += UPD_WARPS) {
+            df v = {0.0f, 0.0f};
+            for (int q = 0; q < UPD_WARPS; ++q) v = v + df_of(pe[(q * MOM_SUMS + j) * TILE + lane]);
+            const double d = (double)v.hi + (double)v.lo;
+            if (G > 1) {
+                if (valid) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = d;
+            } else {
+                ss[j * TILE + lane] = d;
+            }
+        }
+    } else {
+        double o[MOM_SUMS];
+#pragma unroll
+        for (int j = 0; j < MOM_SUMS; ++j) o[j] = 0.0;
+        for (int kx = kxa + wy; kx <= kxb; kx += UPD_WARPS) {
+            const int ta = max(0, k0 - kx * Tc), tb = min(Tc, k1 - kx * Tc);
+            InnerSum<double> a[NTW];
+            for (int t = ta; t < tb; ++t) {
+                const double fv = fo[(kx * Tc + t - k0) * TILE + lane];
+#pragma unroll
+                for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], 0.0f, 0.0f);
+            }
+            double Sv[NTW];
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) Sv[j] = a[j].value();
+            outer_sums(o, Sv, I.px[kx], kx >= Q);
+        }
+#pragma unroll
+        for (int j = 0; j < MOM_SUMS; ++j) ex[(wy * MOM_SUMS + j) * TILE + lane] = o[j];
+        __syncthreads();
+        for (int j = wy; j < MOM_SUMS; j += UPD_WARPS) {
+            double v = 0.0;
+            for (int q = 0; q < UPD_WARPS; ++q) v += ex[(q * MOM_SUMS + j) * TILE + lane];
+            if (G > 1) {
+                if (valid) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = v;
+            } else {
+                ss[j * TILE + lane] = v;
+            }
+        }
+    }
+    if (G > 1) return;
+    __syncthreads();
+    const int tid = wy * TILE + lane;
+    if (tid < 128) finalize_tile(I, i0, ss, tid);
+}
+
+// Tiled schedule, tiles split into several chunks: the last chunk block of the tile to arrive
+// (ticket) adds the chunks' partial sums in chunk order -- the result does not depend on the
+// arrival order -- and resets the ticket.  ss: MOM_SUMS x TILE shared doubles.
+__device__ void chunk_ticket_final(const Inst& I, int i0, double* ss) {
+    __shared__ int last;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, tile = i0 / TILE;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(I.mcnt + tile, 1) == I.mgroups - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid == 0) I.mcnt[tile] = 0;
+    if (tid < 128) moments_final_tile(I, i0, ss, tid, 1);
+}
+
 // Velocities [k0, k1) of one tile for RK stage `stage`, by UPD_WARPS warps (lane, warp wy);
-// smem_raw holds the tile's table (ntab x TILE values of C).
+// smem_raw holds upd_smem_bytes(ntab, ukc, sizeof(C), sizeof(S)).  The epilogue computes the
+// moments of the new values (chunk_moments).
 template <typename S, typename C>
 __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, unsigned char* smem_raw, int lane, int wy) {
     C* stab = reinterpret_cast<C*>(smem_raw);
+    S* fo = reinterpret_cast<S*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)));
+    double* ex = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(fo) + (size_t)I.ukc * TILE * sizeof(S));
     const int i = i0 + lane;
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, ntab = I.ntab;
     const bool valid = i < N;
@@ -1386,7 +1322,10 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
             if (i == 0) fl = pos ? nwL * gLc[k] : (11 * v[3] - 7 * v[4] + 2 * v[5]) * sixth;
             else fl = pos ? weno_face(v[0], v[1], v[2], v[3], v[4]) : weno_face(v[5], v[4], v[3], v[2], v[1]);
         }
-        if (!valid) continue;
+        if (!valid) {
+            fo[(k - k0) * TILE + lane] = (S)0;
+            continue;
+        }
         C L = -xpi * p * (fr - fl);
         if (force) {
             const int ky = t / Tz, kz = t - ky * Tz;
@@ -1403,7 +1342,10 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
         C out = cb * (fi + dt * L);
         if (stage != 1) out += ca * (C)F[(size_t)k * ld + i];
         dst[(size_t)k * ld + i] = (S)out;
+        fo[(k - k0) * TILE + lane] = (S)out;
     }
+    __syncthreads();
+    chunk_moments<S>(I, i0, k0, k1, k0 / I.ukc, fo, ex, lane, wy);
 }
 
 template <typename S, typename C>
@@ -1414,6 +1356,30 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     if (*I.status != FDLB_ACTIVE) return;
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     update_item<S, C>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y);
+    if (I.mgroups > 1)
+        chunk_ticket_final(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)) +
+                                                              (size_t)I.ukc * TILE * sizeof(S)) + UPD_WARPS * MOM_SUMS * TILE);
+}
+
+// Moments of buffer `buf` from scratch (creation, new profiles, a loaded state): one block per
+// update chunk of a tile with exactly the arithmetic of the update epilogue, so that the
+// moments of a state do not depend on how it was reached (restarts are bitwise).
+template <typename S>
+__global__ void __launch_bounds__(TILE * UPD_WARPS) k_moments(const Inst* __restrict__ insts, const Work* __restrict__ work, int buf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Work w = work[blockIdx.x];
+    const Inst& I = insts[w.inst];
+    if (*I.status != FDLB_ACTIVE) return;
+    if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
+    const int lane = threadIdx.x, wy = threadIdx.y, i = w.i0 + lane, ld = I.ld;
+    const bool valid = i < I.N;
+    S* fo = reinterpret_cast<S*>(smem_raw);
+    double* ex = reinterpret_cast<double*>(smem_raw + (size_t)I.ukc * TILE * sizeof(S));
+    const S* f = static_cast<const S*>(I.f[buf]);
+    for (int k = w.k0 + wy; k < w.k1; k += UPD_WARPS) fo[(k - w.k0) * TILE + lane] = valid ? f[(size_t)k * ld + i] : (S)0;
+    __syncthreads();
+    chunk_moments<S>(I, w.i0, w.k0, w.k1, w.k0 / I.ukc, fo, ex, lane, wy);
+    if (I.mgroups > 1) chunk_ticket_final(I, w.i0, ex + UPD_WARPS * MOM_SUMS * TILE);
 }
 
 // ---------------------------------------------------------------------------
@@ -1427,41 +1393,28 @@ namespace cg = cooperative_groups;
 
 constexpr int RES_THREADS = TILE * NOD_WARPS;    // 256 = UPD_WARPS warps = two moment halves
 
-__host__ __device__ inline size_t resident_smem_bytes(int qmax, int ntab_max) {
-    const size_t mom = (size_t)2 * MOM_SMEM * sizeof(double);
+__host__ __device__ inline size_t resident_smem_bytes(int qmax, size_t upd_max) {
+    const size_t fin = (size_t)2 * MOM_SUMS * TILE * sizeof(double);
     const size_t nod = (size_t)nodal_smem_doubles(qmax) * sizeof(double);
-    const size_t upd = (size_t)ntab_max * TILE * sizeof(double);
-    size_t m = mom > nod ? mom : nod;
-    return m > upd ? m : upd;
+    size_t m = fin > nod ? fin : nod;
+    return m > upd_max ? m : upd_max;
 }
 
-template <typename S>
-__device__ void res_moments(const Inst& I, int buf, int rank, int CS, unsigned char* sm, cg::cluster_group& cl) {
-    const int tiles = (I.N + TILE - 1) / TILE, G = I.mgroups;
-    const int half = threadIdx.x >> 7;
-    double* part = reinterpret_cast<double*>(sm) + half * MOM_SMEM;
-    for (int it = 2 * rank + half; it < tiles * G; it += 2 * CS)
-        moments_item<S>(I, (it / G) * TILE, it % G, buf, part, threadIdx.x & 127, 1 + half);
+// Moments of tiles whose update was split into chunks: the chunk partials, by 128-thread halves.
+__device__ void res_final(const Inst& I, int rank, int CS, unsigned char* sm, cg::cluster_group& cl) {
+    const int tiles = (I.N + TILE - 1) / TILE, half = threadIdx.x >> 7;
+    double* ss = reinterpret_cast<double*>(sm) + half * MOM_SUMS * TILE;
+    for (int tl = 2 * rank + half; tl < tiles; tl += 2 * CS) moments_final_tile(I, tl * TILE, ss, threadIdx.x & 127, 1 + half);
     cl.sync();
-    if (G > 1) {
-        for (int tl = 2 * rank + half; tl < tiles; tl += 2 * CS)
-            moments_final_tile(I, tl * TILE, part, threadIdx.x & 127, 1 + half);
-        cl.sync();
-    }
 }
 
 template <int QB, typename S>
 __device__ void res_step(Inst& I, int idx, double tol, double* resid_all, int rank, int CS, unsigned char* sm,
                          cg::cluster_group& cl) {
-    const int tiles = (I.N + TILE - 1) / TILE, K = I.K;
-    // velocity chunks of the update items: about two items per CTA
-    int nch = (2 * CS + tiles - 1) / tiles;
-    nch = nch < 1 ? 1 : (nch > (K + UPD_WARPS - 1) / UPD_WARPS ? (K + UPD_WARPS - 1) / UPD_WARPS : nch);
-    const int KC = ((K + nch - 1) / nch + UPD_WARPS - 1) / UPD_WARPS * UPD_WARPS;
-    nch = (K + KC - 1) / KC;
+    const int tiles = (I.N + TILE - 1) / TILE, K = I.K, KC = I.ukc, nch = I.mgroups;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    // the update items' epilogue computes the moments of each stage's result
     for (int stage = 1; stage <= 3; ++stage) {
-        if (stage > 1) res_moments<S>(I, stage - 1, rank, CS, sm, cl);
         for (int it = rank; it < 3 * tiles; it += CS)
             nodal_item<QB>(I, (it / 3) * TILE, it % 3, reinterpret_cast<double*>(sm), sizeof(S) == 4);
         cl.sync();
@@ -1470,8 +1423,8 @@ __device__ void res_step(Inst& I, int idx, double tol, double* resid_all, int ra
             update_item<S, S>(I, tl * TILE, k0, min(K, k0 + KC), stage, sm, lane, wy);
         }
         cl.sync();
+        if (nch > 1) res_final(I, rank, CS, sm, cl);
     }
-    res_moments<S>(I, 0, rank, CS, sm, cl);
     if (rank == 0) resid_item(I, idx, tol, resid_all);
 }
 
@@ -1518,9 +1471,27 @@ cudaError_t launch_set_profiles(const Inst* d_inst, int inst, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const Inst* d_inst, const Work* d_mom, int n_mom, int buf, bool f64, bool f32, cudaStream_t s) {
-    if (f64) k_moments<double><<<n_mom, TILE * MOM3_WARPS, 0, s>>>(d_inst, d_mom, buf);
-    if (f32) k_moments<float><<<n_mom, TILE * MOM3_WARPS, 0, s>>>(d_inst, d_mom, buf);
+size_t moments_smem_bytes(int ukc, size_t s) { return (size_t)ukc * TILE * s + (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double); }
+
+size_t update_smem_bytes(int ntab, int ukc, size_t c, size_t s) { return upd_smem_bytes(ntab, ukc, c, s); }
+
+cudaError_t launch_moments(const Inst* d_inst, const Work* d_upd, int n_upd, int buf, int ukc_max, bool f64, bool f32,
+                           cudaStream_t s) {
+    static size_t done64 = 0, done32 = 0;
+    const size_t m64 = moments_smem_bytes(ukc_max, 8), m32 = moments_smem_bytes(ukc_max, 4);
+    cudaError_t e = cudaSuccess;
+    if (f64 && m64 > 48 * 1024 && m64 > done64) {
+        e = cudaFuncSetAttribute(k_moments<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m64);
+        if (e == cudaSuccess) done64 = m64;
+    }
+    if (e == cudaSuccess && f32 && m32 > 48 * 1024 && m32 > done32) {
+        e = cudaFuncSetAttribute(k_moments<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m32);
+        if (e == cudaSuccess) done32 = m32;
+    }
+    if (e != cudaSuccess) return e;
+    dim3 blk(TILE, UPD_WARPS);
+    if (f64) k_moments<double><<<n_upd, blk, m64, s>>>(d_inst, d_upd, buf);
+    if (f32) k_moments<float><<<n_upd, blk, m32, s>>>(d_inst, d_upd, buf);
     return cudaGetLastError();
 }
 
@@ -1592,8 +1563,8 @@ static cudaError_t resident_config(size_t smem, int cs) {
     return e;
 }
 
-cudaError_t prepare_resident(int qmax, int ntab_max, int cs, size_t* smem) {
-    *smem = resident_smem_bytes(qmax, ntab_max);
+cudaError_t prepare_resident(int qmax, size_t upd_max, int cs, size_t* smem) {
+    *smem = resident_smem_bytes(qmax, upd_max);
     return qmax <= 8 ? resident_config<8>(*smem, cs) : resident_config<QMAX>(*smem, cs);
 }
 

@@ -8,9 +8,15 @@ namespace fdlb {
 // Wall Maxwellians, initial uniform equilibrium, status/steps reset, for all instances.
 cudaError_t launch_setup(const Inst* d_inst, int count, cudaStream_t s);
 
-// Moments of RK buffer `buf` (0 = F, 1 = A, 2 = B) of every ACTIVE instance.
-cudaError_t launch_moments(const Inst* d_inst, const Work* d_mom, int n_mom, int buf, bool f64, bool f32,
+// Moments of RK buffer `buf` (0 = F, 1 = A, 2 = B) of every ACTIVE instance from scratch
+// (during steps the update kernel's epilogue computes them): one block per update work item;
+// ukc_max = largest update chunk of the batch.  Not inside a stream capture (it may set a
+// kernel attribute).
+cudaError_t launch_moments(const Inst* d_inst, const Work* d_upd, int n_upd, int buf, int ukc_max, bool f64, bool f32,
                            cudaStream_t s);
+
+// Shared memory of one update item (table of ntab rows in type size c, ukc outputs of size s).
+size_t update_smem_bytes(int ntab, int ukc, size_t c, size_t s);
 
 // Residual / status pass after a step (anchor_inst = -2), or re-anchor instance `anchor_inst`
 // (-1 = all): previous moments := current, residual := +inf, without a status change.
@@ -28,8 +34,9 @@ cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int 
                           bool f64, bool f32, cudaStream_t s);
 
 // Resident schedule: attributes (shared memory, cluster size cs) of the cluster kernel for
-// the batch's largest half-range order and table; *smem receives its dynamic shared memory.
-cudaError_t prepare_resident(int qmax, int ntab_max, int cs, size_t* smem);
+// the batch's largest half-range order and update-item shared memory; *smem receives its
+// dynamic shared memory.
+cudaError_t prepare_resident(int qmax, size_t upd_max, int cs, size_t* smem);
 
 // Clusters of cs CTAs that can be resident at once.
 cudaError_t resident_max_clusters(int qmax, size_t smem, int cs, int* n);
