@@ -464,14 +464,53 @@ def run_fdlb(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(case, precision):
+    """Small fixed workloads for ncu captures (no timing, no JSON line).
+    couette1 / couette12: one instance (eta0 = 0.2, Kn = 0.5) or the whole Couette sweep, tiled
+    schedule: creation (5 launches), 20 steps (7 launches each), 3 more steps.
+    mlp: the warm-start network on 32768 points, 6 training steps and one prediction."""
+    import torch
+    from paper_2308_15407_gb300 import fdlb as F
+    if not os.path.exists(F.LIB_PATH):
+        from paper_2308_15407_gb300 import build
+        build.build()
+    if case == "mlp":
+        P = 32768
+        g = torch.Generator(device="cuda").manual_seed(5)
+        X = torch.randn(P, 16, device="cuda", generator=g) * 0.5
+        Y = torch.randn(P, 3, device="cuda", generator=g) * 0.1
+        net = F.MLP(max_points=P, seed=1)
+        for _ in range(6):
+            net.train_step(X, Y, 1e-3)
+        net.predict(X)
+        torch.cuda.synchronize()
+        print("ok")
+        return
+    ps = couette_params(F, precision)
+    if case == "couette1":
+        ps = ps[4:5]
+    s = F.Solver(ps)
+    s.set_schedule("tiled")
+    s.step(20)
+    torch.cuda.synchronize()
+    s.step(3)
+    torch.cuda.synchronize()
+    print("ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fdlb", choices=["fdlb", "reference"])
+    ap.add_argument("--profile-case", choices=["couette1", "couette12", "mlp"], default=None,
+                    help="run a small fixed workload for an ncu capture instead of the benchmark")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args.profile_case, args.precision)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_fdlb(args)
