@@ -1151,10 +1151,29 @@ struct Tabs<float> {
     __device__ static const float* Ky(const Inst& I) { return I.Ky32; }
 };
 
-// Shared memory of one update item: table, the chunk's outputs, per-warp moment sums, sums.
+// Shared memory of one update item: table, transverse moment weights, the chunk's outputs,
+// per-warp moment sums, sums.
+constexpr size_t TW_BYTES = (size_t)NTW * TCMAX * sizeof(double);
 __host__ __device__ inline size_t upd_table_bytes(int ntab, size_t c) { return ((size_t)ntab * TILE * c + 15) / 16 * 16; }
 __host__ __device__ inline size_t upd_smem_bytes(int ntab, int ukc, size_t c, size_t s) {
-    return upd_table_bytes(ntab, c) + (size_t)ukc * TILE * s + (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double);
+    return upd_table_bytes(ntab, c) + TW_BYTES + (size_t)ukc * TILE * s + (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double);
+}
+
+// Transverse moment weights of the epilogue into shared memory (FP32 storage: float heads
+// and tails, FP64: doubles), by the whole block.
+template <typename S>
+__device__ __forceinline__ void load_tw(const Inst& I, void* tws, int tid, int nthreads) {
+    const int n = NTW * I.Tc;
+    if constexpr (sizeof(S) == 4) {
+        float* h = static_cast<float*>(tws);
+        for (int e = tid; e < n; e += nthreads) {
+            h[e] = I.twh[e];
+            h[n + e] = I.twl[e];
+        }
+    } else {
+        double* d = static_cast<double*>(tws);
+        for (int e = tid; e < n; e += nthreads) d[e] = I.tw[e];
+    }
 }
 
 // Epilogue of an update item: raw moment sums of the chunk's values fo[k - k0][lane] with the
@@ -1162,7 +1181,8 @@ __host__ __device__ inline size_t upd_smem_bytes(int ntab, int ukc, size_t c, si
 // x-velocities; FP32 pairs and double-float for FP32 storage), summed over the warps, then
 // the moments (one chunk per tile) or the chunk's partial sums in msum[grp].
 template <typename S>
-__device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, const S* fo, double* ex, int lane, int wy) {
+__device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, const S* fo, double* ex, const void* tws,
+                              int lane, int wy) {
     const int i = i0 + lane, ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
     const bool valid = i < I.N;
     const int kxa = k0 / Tc, kxb = (k1 - 1) / Tc;
@@ -1173,11 +1193,13 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
         for (int j = 0; j < MOM_SUMS; ++j) o[j] = {0.0f, 0.0f};
         for (int kx = kxa + wy; kx <= kxb; kx += UPD_WARPS) {
             const int ta = max(0, k0 - kx * Tc), tb = min(Tc, k1 - kx * Tc);
+            const float* twh = static_cast<const float*>(tws);
+            const float* twl = twh + NTW * Tc;
             InnerSum<float> a[NTW];
             for (int t = ta; t < tb; ++t) {
                 const float fv = fo[(kx * Tc + t - k0) * TILE + lane];
 #pragma unroll
-                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, I.twh[j * Tc + t], I.twl[j * Tc + t]);
+                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, twh[j * Tc + t], twl[j * Tc + t]);
             }
             df Sd[NTW];
 #pragma unroll
@@ -1204,11 +1226,12 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
         for (int j = 0; j < MOM_SUMS; ++j) o[j] = 0.0;
         for (int kx = kxa + wy; kx <= kxb; kx += UPD_WARPS) {
             const int ta = max(0, k0 - kx * Tc), tb = min(Tc, k1 - kx * Tc);
+            const double* tw = static_cast<const double*>(tws);
             InnerSum<double> a[NTW];
             for (int t = ta; t < tb; ++t) {
                 const double fv = fo[(kx * Tc + t - k0) * TILE + lane];
 #pragma unroll
-                for (int j = 0; j < NTW; ++j) a[j].add(fv, I.tw[j * Tc + t], 0.0f, 0.0f);
+                for (int j = 0; j < NTW; ++j) a[j].add(fv, tw[j * Tc + t], 0.0f, 0.0f);
             }
             double Sv[NTW];
 #pragma unroll
@@ -1256,7 +1279,8 @@ __device__ void chunk_ticket_final(const Inst& I, int i0, double* ss) {
 template <typename S, typename C>
 __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, unsigned char* smem_raw, int lane, int wy) {
     C* stab = reinterpret_cast<C*>(smem_raw);
-    S* fo = reinterpret_cast<S*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)));
+    void* tws = smem_raw + upd_table_bytes(I.ntab, sizeof(C));
+    S* fo = reinterpret_cast<S*>(static_cast<unsigned char*>(tws) + TW_BYTES);
     double* ex = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(fo) + (size_t)I.ukc * TILE * sizeof(S));
     const int i = i0 + lane;
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, ntab = I.ntab;
@@ -1268,6 +1292,7 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const C* Kyc = Tabs<C>::Ky(I);
     __syncthreads();                      // the previous item's readers of the table are done
     for (int r = wy; r < ntab; r += UPD_WARPS) stab[r * TILE + lane] = valid ? tabc[(size_t)r * ld + i] : (C)0;
+    load_tw<S>(I, tws, wy * TILE + lane, UPD_WARPS * TILE);
     __syncthreads();
     const S* src = static_cast<const S*>(I.f[stage - 1]);
     S* dst = static_cast<S*>(I.f[stage % 3]);
@@ -1282,14 +1307,11 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const int Tz = I.form == FORM_UNREDUCED ? I.Qz : 2;
     const C ay = (C)I.accel_y;
     const C sixth = (C)(1.0 / 6.0);
-    for (int k = k0 + wy; k < k1; k += UPD_WARPS) {
-        const int kx = k / Tc, t = k - kx * Tc;
-        const bool pos = kx < Q;
-        const C p = pxc[kx];
+    // node values i-3 .. i+3 of velocity k with ghost cells (Sec. III B): incoming populations
+    // take the wall Maxwellian n_w g; outgoing ones the quadratic extrapolation of nodes 0..2
+    auto gather = [&](int k, C* v) {
+        const bool pos = k / Tc < Q;
         const S* row = src + (size_t)k * ld;
-        // node values i-3 .. i+3 with ghost cells (Sec. III B): incoming populations take the
-        // wall Maxwellian n_w g; outgoing ones the quadratic extrapolation of nodes 0..2.
-        C v[7];
 #pragma unroll
         for (int jj = 0; jj < 7; ++jj) {
             const int j = i - 3 + jj;
@@ -1312,6 +1334,25 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
                 }
             }
             v[jj] = val;
+        }
+    };
+    // the loads of the warp's next velocity are issued before the current one is computed
+    C vn[7], Fn = 0;
+    if (k0 + wy < k1) {
+        gather(k0 + wy, vn);
+        if (stage != 1 && valid) Fn = (C)F[(size_t)(k0 + wy) * ld + i];
+    }
+    for (int k = k0 + wy; k < k1; k += UPD_WARPS) {
+        const int kx = k / Tc, t = k - kx * Tc;
+        const bool pos = kx < Q;
+        const C p = pxc[kx];
+        C v[7];
+#pragma unroll
+        for (int jj = 0; jj < 7; ++jj) v[jj] = vn[jj];
+        const C Fk = Fn;
+        if (k + UPD_WARPS < k1) {
+            gather(k + UPD_WARPS, vn);
+            if (stage != 1 && valid) Fn = (C)F[(size_t)(k + UPD_WARPS) * ld + i];
         }
         // right face (i + 1/2)
         C fr;
@@ -1340,12 +1381,12 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
         const C fi = v[3];
         L += (tgt - fi) * invtau;
         C out = cb * (fi + dt * L);
-        if (stage != 1) out += ca * (C)F[(size_t)k * ld + i];
+        if (stage != 1) out += ca * Fk;
         dst[(size_t)k * ld + i] = (S)out;
         fo[(k - k0) * TILE + lane] = (S)out;
     }
     __syncthreads();
-    chunk_moments<S>(I, i0, k0, k1, k0 / I.ukc, fo, ex, lane, wy);
+    chunk_moments<S>(I, i0, k0, k1, k0 / I.ukc, fo, ex, tws, lane, wy);
 }
 
 template <typename S, typename C>
@@ -1357,7 +1398,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     update_item<S, C>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y);
     if (I.mgroups > 1)
-        chunk_ticket_final(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)) +
+        chunk_ticket_final(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)) + TW_BYTES +
                                                               (size_t)I.ukc * TILE * sizeof(S)) + UPD_WARPS * MOM_SUMS * TILE);
 }
 
@@ -1373,12 +1414,14 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_moments(const Inst* __rest
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     const int lane = threadIdx.x, wy = threadIdx.y, i = w.i0 + lane, ld = I.ld;
     const bool valid = i < I.N;
-    S* fo = reinterpret_cast<S*>(smem_raw);
-    double* ex = reinterpret_cast<double*>(smem_raw + (size_t)I.ukc * TILE * sizeof(S));
+    void* tws = smem_raw;
+    S* fo = reinterpret_cast<S*>(smem_raw + TW_BYTES);
+    double* ex = reinterpret_cast<double*>(smem_raw + TW_BYTES + (size_t)I.ukc * TILE * sizeof(S));
     const S* f = static_cast<const S*>(I.f[buf]);
     for (int k = w.k0 + wy; k < w.k1; k += UPD_WARPS) fo[(k - w.k0) * TILE + lane] = valid ? f[(size_t)k * ld + i] : (S)0;
+    load_tw<S>(I, tws, wy * TILE + lane, UPD_WARPS * TILE);
     __syncthreads();
-    chunk_moments<S>(I, w.i0, w.k0, w.k1, w.k0 / I.ukc, fo, ex, lane, wy);
+    chunk_moments<S>(I, w.i0, w.k0, w.k1, w.k0 / I.ukc, fo, ex, tws, lane, wy);
     if (I.mgroups > 1) chunk_ticket_final(I, w.i0, ex + UPD_WARPS * MOM_SUMS * TILE);
 }
 
@@ -1471,7 +1514,9 @@ cudaError_t launch_set_profiles(const Inst* d_inst, int inst, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-size_t moments_smem_bytes(int ukc, size_t s) { return (size_t)ukc * TILE * s + (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double); }
+size_t moments_smem_bytes(int ukc, size_t s) {
+    return TW_BYTES + (size_t)ukc * TILE * s + (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double);
+}
 
 size_t update_smem_bytes(int ntab, int ukc, size_t c, size_t s) { return upd_smem_bytes(ntab, ukc, c, s); }
 
