@@ -931,11 +931,13 @@ __device__ int stagnated(Inst& I, double r, double step) {
 __device__ void resid_item(Inst& I, int idx, double tol, double* resid_all) {
     const int ld = I.ld, N = I.N;
     double* nd = I.node;
-    __shared__ double red[7][8];
+    constexpr int RT = 256;                   // threads of the calling block
+    __shared__ double red[7][RT];
+    __shared__ double tot[7], term[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
     int bad_nf = 0, bad_ph = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    for (int i = threadIdx.x; i < N; i += RT) {
         const double n = nd[R_N * ld + i], ux = nd[R_UX * ld + i], uy = nd[R_UY * ld + i], T = nd[R_T * ld + i];
         if (!isfinite(n) || !isfinite(ux) || !isfinite(uy) || !isfinite(T)) bad_nf = 1;
         else if (!(n > 0.0) || !(T > 0.0)) bad_ph = 1;
@@ -957,23 +959,26 @@ __device__ void resid_item(Inst& I, int idx, double tol, double* resid_all) {
     __shared__ int flags[3];
     __shared__ double scale;
     if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
+#pragma unroll
+    for (int j = 0; j < 7; ++j) red[j][threadIdx.x] = s[j];
     __syncthreads();
     if (bad_nf) atomicOr(&flags[0], 1);
     if (bad_ph) atomicOr(&flags[1], 1);
+    // sum j over the block by warp j (independent FP64 chains on different schedulers)
+    if (wid < 7) {
+        double v = 0.0;
 #pragma unroll
-    for (int j = 0; j < 7; ++j) {
-        double v = s[j];
+        for (int q = 0; q < RT / 32; ++q) v += red[wid][q * 32 + lane];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[j][wid] = v;
+        if (lane == 0) tot[wid] = v;
     }
     __syncthreads();
+    // the four terms of the residual on four warps
+    if (lane == 0 && wid < 4)
+        term[wid] = wid == 0 ? sqrt(tot[0] / tot[1]) : (wid == 1 ? sqrt(tot[2] / tot[3]) : sqrt(tot[wid + 2]));
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double t[7];
-        for (int j = 0; j < 7; ++j) {
-            t[j] = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t[j] += red[j][q];
-        }
-        double r = fmax(fmax(sqrt(t[0] / t[1]), sqrt(t[2] / t[3])), fmax(sqrt(t[4]), sqrt(t[5])));
+        double r = fmax(fmax(term[0], term[1]), fmax(term[2], term[3]));
         *I.steps += 1;
         I.misc[M_RESID] = r;
         resid_all[idx] = r;
@@ -984,7 +989,7 @@ __device__ void resid_item(Inst& I, int idx, double tol, double* resid_all) {
         else if (fp32 && r == 0.0 && tol > 0.0) *I.status = FDLB_STAGNATED;
         else if (tol > 0.0 && r < tol) *I.status = FDLB_CONVERGED;
         else if (I.two_phase && fp32) flags[2] = stagnated(I, r, (double)*I.steps);
-        scale = I.misc[M_MASS0] / t[6];
+        scale = I.misc[M_MASS0] / tot[6];
     }
     __syncthreads();
     if (!flags[2]) return;
