@@ -508,7 +508,7 @@ __device__ __forceinline__ df df_exp(df z) {
 
 // Half-range x projection of an FP32-storage tile (roles 0 / 1 of nodal_item) in double-float:
 // the same steps as the FP64 branch, with the per-node scalars sqrt(T), u and v computed once
-// in FP64 by warp 0 and shared.
+// by warp 0 and shared.
 template <int QB>
 __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -518,17 +518,25 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
     __shared__ float2 xs[4][TILE];                   // sqrt(T), u, v, v^2/2 as pairs
     __shared__ int use_short;
     if (wid == 0) {
-        const double T = I.node[R_T * ld + ic], ux = I.node[R_UX * ld + ic];
-        const double sT = sqrt(T), uu = role ? -ux : ux, v = uu / sT;
-        const df a = df_of(sT), b = df_of(uu), c = df_of(v), d = df_of(0.5 * v * v);
-        xs[0][lane] = make_float2(a.hi, a.lo);
-        xs[1][lane] = make_float2(b.hi, b.lo);
-        xs[2][lane] = make_float2(c.hi, c.lo);
+        // sqrt T and u / sqrt T in double-float: one Newton correction of the FP32 root and
+        // quotient (both ~1e-14)
+        const double ux = I.node[R_UX * ld + ic];
+        const df T = df_of(I.node[R_T * ld + ic]), uu = df_of(role ? -ux : ux);
+        const float s0 = sqrtf(T.hi);
+        const df r0 = T - df{s0, 0.0f} * df{s0, 0.0f};
+        const df sT = df_fast(s0, __fdiv_rn(r0.hi, 2.0f * s0));
+        const float q0 = __fdiv_rn(uu.hi, sT.hi);
+        const df r1 = uu - df{q0, 0.0f} * sT;
+        const df v = df_fast(q0, __fdiv_rn(r1.hi, sT.hi));
+        const df d = df{0.5f, 0.0f} * v * v;
+        xs[0][lane] = make_float2(sT.hi, sT.lo);
+        xs[1][lane] = make_float2(uu.hi, uu.lo);
+        xs[2][lane] = make_float2(v.hi, v.lo);
         xs[3][lane] = make_float2(d.hi, d.lo);
-        double av = valid ? fabs(v) : 0.0;
+        float av = valid ? fabsf(v.hi) : 0.0f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
-        if (lane == 0) use_short = av < 0.02 ? 1 : 2;
+        for (int o = 16; o > 0; o >>= 1) av = fmaxf(av, __shfl_xor_sync(0xffffffffu, av, o));
+        if (lane == 0) use_short = av < 0.02f ? 1 : 2;
     }
     __syncthreads();
     const bool short_rule = use_short == 1 && Q <= 12;
@@ -599,8 +607,6 @@ __device__ __forceinline__ double r_tab(const double* d, const float2*, int k, d
 __device__ __forceinline__ df r_tab(const double*, const float2* p, int k, df) { return df_of(p[k]); }
 __device__ __forceinline__ double r_dbl(double x) { return x; }
 __device__ __forceinline__ double r_dbl(df x) { return (double)x.hi + (double)x.lo; }
-__device__ __forceinline__ void r_store(const Inst& I, size_t r, double v) { I.tab[r] = v; }
-__device__ __forceinline__ void r_store(const Inst& I, size_t r, df v) { I.tab32[r] = df_float(v); }
 
 // Full-range projection row a of (p - u0)^a g on the Qn nodes (App. A): sum over the auxiliary
 // rule (M points) of w (p - u0)^a h_l(p), then the H matrix.  R: arithmetic type.
@@ -628,14 +634,23 @@ __device__ void full_row(int a, int Qn, int M, const double* aq, const double* a
             }
         }
     }
-    for (int k2 = 0; k2 < Qn; ++k2) {
-        R t = zero;
 #pragma unroll
-        for (int l = 0; l < QYMAX; ++l)
-            if (l < Qn) t = r_tab(H, H2, l * Qn + k2, R{}) * G[l] + t;
-        P[k2 * TILE + lane] = t;
+    for (int k2 = 0; k2 < QYMAX; ++k2) {
+        if (k2 < Qn) {
+            R t = zero;
+#pragma unroll
+            for (int l = 0; l < QYMAX; ++l)
+                if (l < Qn) t = r_tab(H, H2, l * Qn + k2, R{}) * G[l] + t;
+            P[k2 * TILE + lane] = t;
+        }
     }
 }
+
+// Output rows of the projection table in the closure's arithmetic type.
+__device__ __forceinline__ double* r_out(const Inst& I, double) { return I.tab; }
+__device__ __forceinline__ float* r_out(const Inst& I, df) { return I.tab32; }
+__device__ __forceinline__ void r_put(double* p, size_t r, double v) { p[r] = v; }
+__device__ __forceinline__ void r_put(float* p, size_t r, df v) { p[r] = df_float(v); }
 
 // Role 2 of a tile: gradients (Sec. III B 3), closure (Eqs. chi, prandtl, viscosity, tau), the
 // 13 coefficients of f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j) (Eq. j1), the y and z
@@ -748,24 +763,39 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
         }
     }
     __syncthreads();
-    if (I.form != FORM_REDUCED1D) {
-        // A[a][c'][ky] = n sum over monomials (a, b, c = 2 c') of coef * Py[b][ky]
-        for (int o = wid; o < 8 * Qy; o += NOD_WARPS) {
-            const int ac = o / Qy, ky = o - ac * Qy, a = ac >> 1, c2 = ac & 1;
-            R t = r_of(0.0, R{});
-            for (int j = 0; j < NTERMS; ++j)
-                if (c_mono[j][0] == a && c_mono[j][2] == 2 * c2) t = sc[j * TILE + lane] * Py[(c_mono[j][1] * QYMAX + ky) * TILE + lane] + t;
-            Ay[o * TILE + lane] = sc[13 * TILE + lane] * t;
+    auto* out = r_out(I, R{});
+    const int form = I.form;
+    if (form != FORM_REDUCED1D) {
+        // A[a][c'][ky] = n sum over the monomials (a, b, c = 2 c') of coef * Py[b][ky]; with the
+        // monomial order of c_mono: (0,0,0) (1,0,0) (0,1,0) (2,0,0) (0,2,0) (0,0,2) (1,1,0)
+        // (3,0,0) (1,2,0) (1,0,2) (2,1,0) (0,3,0) (0,1,2)
+        for (int ky = wid; ky < Qy; ky += NOD_WARPS) {
+            R c[NTERMS];
+#pragma unroll
+            for (int j = 0; j < NTERMS; ++j) c[j] = sc[j * TILE + lane];
+            const R n = sc[13 * TILE + lane];
+            const R P0 = Py[(0 * QYMAX + ky) * TILE + lane], P1 = Py[(1 * QYMAX + ky) * TILE + lane];
+            const R P2 = Py[(2 * QYMAX + ky) * TILE + lane], P3 = Py[(3 * QYMAX + ky) * TILE + lane];
+            const R zero = r_of(0.0, R{});
+            Ay[(0 * Qy + ky) * TILE + lane] = n * (c[0] * P0 + c[2] * P1 + c[4] * P2 + c[11] * P3);   // a = 0, c' = 0
+            Ay[(1 * Qy + ky) * TILE + lane] = n * (c[5] * P0 + c[12] * P1);                          // a = 0, c' = 1
+            Ay[(2 * Qy + ky) * TILE + lane] = n * (c[1] * P0 + c[6] * P1 + c[8] * P2);               // a = 1, c' = 0
+            Ay[(3 * Qy + ky) * TILE + lane] = n * (c[9] * P0);                                       // a = 1, c' = 1
+            Ay[(4 * Qy + ky) * TILE + lane] = n * (c[3] * P0 + c[10] * P1);                          // a = 2, c' = 0
+            Ay[(5 * Qy + ky) * TILE + lane] = zero;                                                  // a = 2, c' = 1
+            Ay[(6 * Qy + ky) * TILE + lane] = n * (c[7] * P0);                                       // a = 3, c' = 0
+            Ay[(7 * Qy + ky) * TILE + lane] = zero;                                                  // a = 3, c' = 1
         }
         __syncthreads();
         // transverse factors n Y[a][t] = A[a][0][ky] Z0(t) + A[a][1][ky] Z2(t)
         const double T = nd[R_T * ld + ic];
         const R Tr = r_of(T, R{}), one = r_of(1.0, R{}), T23 = r_of(3.0 * T * T, R{});
+#pragma unroll 4
         for (int o = wid; o < 4 * Tc; o += NOD_WARPS) {
             const int a = o / Tc, t = o - a * Tc;
             R z0, z2;
             int ky;
-            if (I.form == FORM_UNREDUCED) {
+            if (form == FORM_UNREDUCED) {
                 ky = t / Qz;
                 const int kz = t - ky * Qz;
                 z0 = Pz[(0 * QZMAX + kz) * TILE + lane];
@@ -777,7 +807,7 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
                 z2 = theta ? T23 : Tr;
             }
             const R v = Ay[((2 * a) * Qy + ky) * TILE + lane] * z0 + Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2;
-            if (valid) r_store(I, (size_t)(8 * Q + a * Tc + t) * ld + i, v);
+            if (valid) r_put(out, (size_t)(8 * Q + a * Tc + t) * ld + i, v);
         }
     } else {
         // 1D reduced (Sec. II B 1): slots phi, theta carry the (p_y, p_z) Gaussian moments
@@ -790,9 +820,9 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
             const double e = slot == 0 ? gmom(b, T) * gmom(cc, T) : gmom(b + 2, T) * gmom(cc, T) + gmom(b, T) * gmom(cc + 2, T);
             t = fma(r_dbl(sc[j * TILE + lane]), e, t);
         }
-        if (valid) r_store(I, (size_t)(8 * Q + a * Tc + slot) * ld + i, r_of(r_dbl(sc[13 * TILE + lane]) * t, R{}));
+        if (valid) r_put(out, (size_t)(8 * Q + a * Tc + slot) * ld + i, r_of(r_dbl(sc[13 * TILE + lane]) * t, R{}));
     }
-    if (wid == 0 && valid) r_store(I, (size_t)(8 * Q + 4 * Tc) * ld + i, sc[14 * TILE + lane]);
+    if (wid == 0 && valid) r_put(out, (size_t)(8 * Q + 4 * Tc) * ld + i, sc[14 * TILE + lane]);
 }
 
 // One (tile, role) item by a block of NOD_WARPS warps; nsm holds nodal_smem_doubles(QB)
