@@ -634,7 +634,6 @@ __device__ void full_row(int a, int Qn, int M, const double* aq, const double* a
             }
         }
     }
-#pragma unroll
     for (int k2 = 0; k2 < QYMAX; ++k2) {
         if (k2 < Qn) {
             R t = zero;
@@ -787,27 +786,28 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
             Ay[(7 * Qy + ky) * TILE + lane] = zero;                                                  // a = 3, c' = 1
         }
         __syncthreads();
-        // transverse factors n Y[a][t] = A[a][0][ky] Z0(t) + A[a][1][ky] Z2(t)
+        // transverse factors n Y[a][t] = A[a][0][ky] Z0(t) + A[a][1][ky] Z2(t), t = ky Tz + kz;
+        // a warp takes (a, ky) pairs and runs over kz (no per-output index divisions)
         const double T = nd[R_T * ld + ic];
         const R Tr = r_of(T, R{}), one = r_of(1.0, R{}), T23 = r_of(3.0 * T * T, R{});
-#pragma unroll 4
-        for (int o = wid; o < 4 * Tc; o += NOD_WARPS) {
-            const int a = o / Tc, t = o - a * Tc;
-            R z0, z2;
-            int ky;
-            if (form == FORM_UNREDUCED) {
-                ky = t / Qz;
-                const int kz = t - ky * Qz;
-                z0 = Pz[(0 * QZMAX + kz) * TILE + lane];
-                z2 = Pz[(2 * QZMAX + kz) * TILE + lane];
+        const bool unred = form == FORM_UNREDUCED;
+        const int Tz = unred ? Qz : 2;
+        for (int pr = wid; pr < 4 * Qy; pr += NOD_WARPS) {
+            const int a = pr / Qy, ky = pr - a * Qy;
+            const R A0 = Ay[((2 * a) * Qy + ky) * TILE + lane], A1 = Ay[((2 * a + 1) * Qy + ky) * TILE + lane];
+            auto* row = out + (size_t)(8 * Q + a * Tc + ky * Tz) * ld + i;
+            if (unred) {
+                for (int kz = 0; kz < Qz; ++kz) {
+                    const R v = A0 * Pz[(0 * QZMAX + kz) * TILE + lane] + A1 * Pz[(2 * QZMAX + kz) * TILE + lane];
+                    if (valid) r_put(row, (size_t)kz * ld, v);
+                }
             } else {
-                ky = t >> 1;
-                const bool theta = t & 1;
-                z0 = theta ? Tr : one;
-                z2 = theta ? T23 : Tr;
+                const R v0 = A0 * one + A1 * Tr, v1 = A0 * Tr + A1 * T23;
+                if (valid) {
+                    r_put(row, 0, v0);
+                    r_put(row, (size_t)ld, v1);
+                }
             }
-            const R v = Ay[((2 * a) * Qy + ky) * TILE + lane] * z0 + Ay[((2 * a + 1) * Qy + ky) * TILE + lane] * z2;
-            if (valid) r_put(out, (size_t)(8 * Q + a * Tc + t) * ld + i, v);
         }
     } else {
         // 1D reduced (Sec. II B 1): slots phi, theta carry the (p_y, p_z) Gaussian moments
@@ -1344,8 +1344,7 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const C sixth = (C)(1.0 / 6.0);
     // node values i-3 .. i+3 of velocity k with ghost cells (Sec. III B): incoming populations
     // take the wall Maxwellian n_w g; outgoing ones the quadratic extrapolation of nodes 0..2
-    auto gather = [&](int k, C* v) {
-        const bool pos = k / Tc < Q;
+    auto gather = [&](int k, bool pos, C* v) {
         const S* row = src + (size_t)k * ld;
 #pragma unroll
         for (int jj = 0; jj < 7; ++jj) {
@@ -1372,13 +1371,22 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
         }
     };
     // the loads of the warp's next velocity are issued before the current one is computed
+    // (kx, t) of the warp's velocities k = k0 + wy + UPD_WARPS m, stepped without divisions
+    int kx = (k0 + wy) / Tc, t = (k0 + wy) - kx * Tc;
+    int kxn = kx, tn = t + UPD_WARPS;
+    while (tn >= Tc) { tn -= Tc; ++kxn; }
     C vn[7], Fn = 0;
     if (k0 + wy < k1) {
-        gather(k0 + wy, vn);
+        gather(k0 + wy, kx < Q, vn);
         if (stage != 1 && valid) Fn = (C)F[(size_t)(k0 + wy) * ld + i];
     }
-    for (int k = k0 + wy; k < k1; k += UPD_WARPS) {
-        const int kx = k / Tc, t = k - kx * Tc;
+    auto advance = [&]() {
+        kx = kxn;
+        t = tn;
+        tn += UPD_WARPS;
+        while (tn >= Tc) { tn -= Tc; ++kxn; }
+    };
+    for (int k = k0 + wy; k < k1; k += UPD_WARPS, advance()) {
         const bool pos = kx < Q;
         const C p = pxc[kx];
         C v[7];
@@ -1386,7 +1394,7 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
         for (int jj = 0; jj < 7; ++jj) v[jj] = vn[jj];
         const C Fk = Fn;
         if (k + UPD_WARPS < k1) {
-            gather(k + UPD_WARPS, vn);
+            gather(k + UPD_WARPS, kxn < Q, vn);
             if (stage != 1 && valid) Fn = (C)F[(size_t)(k + UPD_WARPS) * ld + i];
         }
         // right face (i + 1/2)
