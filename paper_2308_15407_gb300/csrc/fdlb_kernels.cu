@@ -1220,14 +1220,17 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
                               int lane, int wy) {
     const int i = i0 + lane, ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
     const bool valid = i < I.N;
-    const int kxa = k0 / Tc, kxb = (k1 - 1) / Tc;
+    // warp wy takes the velocities [ka, kb) of the chunk, cut at x-velocity boundaries
+    const int per = (k1 - k0 + UPD_WARPS - 1) / UPD_WARPS;
+    const int ka = min(k1, k0 + wy * per), kb = min(k1, ka + per);
     double* ss = ex + UPD_WARPS * MOM_SUMS * TILE;
     if constexpr (sizeof(S) == 4) {
         df o[MOM_SUMS];
 #pragma unroll
         for (int j = 0; j < MOM_SUMS; ++j) o[j] = {0.0f, 0.0f};
-        for (int kx = kxa + wy; kx <= kxb; kx += UPD_WARPS) {
-            const int ta = max(0, k0 - kx * Tc), tb = min(Tc, k1 - kx * Tc);
+        for (int kk = ka; kk < kb;) {
+            const int kx = kk / Tc, ta = kk - kx * Tc, tb = min(Tc, kb - kx * Tc);
+            kk = kx * Tc + tb;
             const float* twh = static_cast<const float*>(tws);
             const float* twl = twh + NTW * Tc;
             InnerSum<float> a[NTW];
@@ -1259,8 +1262,9 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
         double o[MOM_SUMS];
 #pragma unroll
         for (int j = 0; j < MOM_SUMS; ++j) o[j] = 0.0;
-        for (int kx = kxa + wy; kx <= kxb; kx += UPD_WARPS) {
-            const int ta = max(0, k0 - kx * Tc), tb = min(Tc, k1 - kx * Tc);
+        for (int kk = ka; kk < kb;) {
+            const int kx = kk / Tc, ta = kk - kx * Tc, tb = min(Tc, kb - kx * Tc);
+            kk = kx * Tc + tb;
             const double* tw = static_cast<const double*>(tws);
             InnerSum<double> a[NTW];
             for (int t = ta; t < tb; ++t) {
@@ -1326,7 +1330,21 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const C* gRc = Tabs<C>::gR(I);
     const C* Kyc = Tabs<C>::Ky(I);
     __syncthreads();                      // the previous item's readers of the table are done
-    for (int r = wy; r < ntab; r += UPD_WARPS) stab[r * TILE + lane] = valid ? tabc[(size_t)r * ld + i] : (C)0;
+    // rows in batches: all loads of a batch are issued before its shared-memory stores
+    constexpr int TB = 16;
+    for (int r0 = wy; r0 < ntab; r0 += UPD_WARPS * TB) {
+        C tmp[TB];
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            const int r = r0 + b * UPD_WARPS;
+            tmp[b] = (valid && r < ntab) ? tabc[(size_t)r * ld + i] : (C)0;
+        }
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            const int r = r0 + b * UPD_WARPS;
+            if (r < ntab) stab[r * TILE + lane] = tmp[b];
+        }
+    }
     load_tw<S>(I, tws, wy * TILE + lane, UPD_WARPS * TILE);
     __syncthreads();
     const S* src = static_cast<const S*>(I.f[stage - 1]);
