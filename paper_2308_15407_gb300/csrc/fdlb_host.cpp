@@ -342,14 +342,15 @@ struct Layout {
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Velocities per update block: small batches split a tile's velocities into chunks of 32 to
-// occupy the GPU; large batches give a block the whole tile (the node table is loaded once),
-// at most 256 velocities (the block keeps its outputs in shared memory for the moments).
+// Velocities per update block: small batches split a tile's velocities into chunks (16 for
+// fewer than 38 tiles, a quarter of the SMs; 32 up to 1216 tiles) to occupy the GPU; large
+// batches give a block the whole tile (the node table is loaded once), at most 256
+// velocities (the block keeps its outputs in shared memory for the moments).
 constexpr int UKC_MAX = 256;
 int upd_chunk(const std::vector<fdlb_params>& ps) {
     long tiles = 0;
     for (auto& p : ps) tiles += (p.nx + TILE - 1) / TILE;
-    return tiles >= 1216 ? UKC_MAX : 32;
+    return tiles >= 1216 ? UKC_MAX : (tiles < 38 ? 16 : 32);
 }
 
 Layout layout_of(const fdlb_params& p, int ukc) {
