@@ -113,7 +113,8 @@ struct Inst {
     double* node;              // [NROWS*ld]
     double* tab;               // [ntab*ld] projection table (see below)
     double* misc;              // [NMISC]
-    double* msum;              // [mgroups][14][ld] partial raw moment sums (mgroups > 1 only)
+    double* msum;              // [mgroups][14][ld] partial raw moment sums (mgroups > 1 only; FP32
+                               // storage keeps them as float pairs in the same space)
     int* mcnt;                 // [tiles] arrival tickets of the update chunks of a tile (zero between uses)
     int* status;
     long long* steps;

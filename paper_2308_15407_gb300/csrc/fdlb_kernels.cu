@@ -458,18 +458,29 @@ __device__ __forceinline__ df df_norm(float h, float l) {
 
 // Moments of tile i0 from the I.mgroups partials of its update chunks, added in chunk order,
 // by 128 threads (barrier `bar`); ss: MOM_SUMS x TILE doubles of shared memory.
-__device__ void moments_final_tile(const Inst& I, int i0, double* ss, int tid, int bar) {
+// nw warps (tid < 32 nw, barrier `bar` over them, nw >= 4) share the sums; FP32 storage keeps
+// the partials as float pairs and adds them in double-float, FP64 storage in FP64.
+template <typename S>
+__device__ void moments_final_tile(const Inst& I, int i0, double* ss, int tid, int nw, int bar) {
     const int lane = tid & 31, g = tid >> 5, i = i0 + lane;
     const int ld = I.ld, G = I.mgroups;
-    named_sync(bar, 128);                 // the previous item's readers of `ss` are done
-    for (int j = g; j < MOM_SUMS; j += MOM3_WARPS) {
+    named_sync(bar, 32 * nw);             // the previous item's readers of `ss` are done
+    for (int j = g; j < MOM_SUMS; j += nw) {
         double v = 0.0;
-        if (i < I.N)
-            for (int q = 0; q < G; ++q) v += __ldcg(I.msum + ((size_t)q * MOM_SUMS + j) * ld + i);
+        if (i < I.N) {
+            if constexpr (sizeof(S) == 4) {
+                const float2* ms = reinterpret_cast<const float2*>(I.msum);
+                df a = {0.0f, 0.0f};
+                for (int q = 0; q < G; ++q) a = a + df_of(__ldcg(ms + ((size_t)q * MOM_SUMS + j) * ld + i));
+                v = (double)a.hi + (double)a.lo;
+            } else {
+                for (int q = 0; q < G; ++q) v += __ldcg(I.msum + ((size_t)q * MOM_SUMS + j) * ld + i);
+            }
+        }
         ss[j * TILE + lane] = v;
     }
-    named_sync(bar, 128);
-    finalize_tile(I, i0, ss, tid);
+    named_sync(bar, 32 * nw);
+    if (tid < 128) finalize_tile(I, i0, ss, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -1251,11 +1262,10 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
         for (int j = wy; j < MOM_SUMS; j += UPD_WARPS) {
             df v = {0.0f, 0.0f};
             for (int q = 0; q < UPD_WARPS; ++q) v = v + df_of(pe[(q * MOM_SUMS + j) * TILE + lane]);
-            const double d = (double)v.hi + (double)v.lo;
             if (G > 1) {
-                if (valid) I.msum[((size_t)grp * MOM_SUMS + j) * ld + i] = d;
+                if (valid) reinterpret_cast<float2*>(I.msum)[((size_t)grp * MOM_SUMS + j) * ld + i] = make_float2(v.hi, v.lo);
             } else {
-                ss[j * TILE + lane] = d;
+                ss[j * TILE + lane] = (double)v.hi + (double)v.lo;
             }
         }
     } else {
@@ -1299,6 +1309,7 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
 // Tiled schedule, tiles split into several chunks: the last chunk block of the tile to arrive
 // (ticket) adds the chunks' partial sums in chunk order -- the result does not depend on the
 // arrival order -- and resets the ticket.  ss: MOM_SUMS x TILE shared doubles.
+template <typename S>
 __device__ void chunk_ticket_final(const Inst& I, int i0, double* ss) {
     __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, tile = i0 / TILE;
@@ -1309,7 +1320,7 @@ __device__ void chunk_ticket_final(const Inst& I, int i0, double* ss) {
     if (!last) return;
     __threadfence();
     if (tid == 0) I.mcnt[tile] = 0;
-    if (tid < 128) moments_final_tile(I, i0, ss, tid, 1);
+    moments_final_tile<S>(I, i0, ss, tid, UPD_WARPS, 1);
 }
 
 // Velocities [k0, k1) of one tile for RK stage `stage`, by UPD_WARPS warps (lane, warp wy);
@@ -1459,7 +1470,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     update_item<S, C>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y);
     if (I.mgroups > 1)
-        chunk_ticket_final(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)) + TW_BYTES +
+        chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)) + TW_BYTES +
                                                               (size_t)I.ukc * TILE * sizeof(S)) + UPD_WARPS * MOM_SUMS * TILE);
 }
 
@@ -1483,7 +1494,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_moments(const Inst* __rest
     load_tw<S>(I, tws, wy * TILE + lane, UPD_WARPS * TILE);
     __syncthreads();
     chunk_moments<S>(I, w.i0, w.k0, w.k1, w.k0 / I.ukc, fo, ex, tws, lane, wy);
-    if (I.mgroups > 1) chunk_ticket_final(I, w.i0, ex + UPD_WARPS * MOM_SUMS * TILE);
+    if (I.mgroups > 1) chunk_ticket_final<S>(I, w.i0, ex + UPD_WARPS * MOM_SUMS * TILE);
 }
 
 // ---------------------------------------------------------------------------
@@ -1505,10 +1516,11 @@ __host__ __device__ inline size_t resident_smem_bytes(int qmax, size_t upd_max) 
 }
 
 // Moments of tiles whose update was split into chunks: the chunk partials, by 128-thread halves.
+template <typename S>
 __device__ void res_final(const Inst& I, int rank, int CS, unsigned char* sm, cg::cluster_group& cl) {
     const int tiles = (I.N + TILE - 1) / TILE, half = threadIdx.x >> 7;
     double* ss = reinterpret_cast<double*>(sm) + half * MOM_SUMS * TILE;
-    for (int tl = 2 * rank + half; tl < tiles; tl += 2 * CS) moments_final_tile(I, tl * TILE, ss, threadIdx.x & 127, 1 + half);
+    for (int tl = 2 * rank + half; tl < tiles; tl += 2 * CS) moments_final_tile<S>(I, tl * TILE, ss, threadIdx.x & 127, 4, 1 + half);
     cl.sync();
 }
 
@@ -1527,7 +1539,7 @@ __device__ void res_step(Inst& I, int idx, double tol, double* resid_all, int ra
             update_item<S, S>(I, tl * TILE, k0, min(K, k0 + KC), stage, sm, lane, wy);
         }
         cl.sync();
-        if (nch > 1) res_final(I, rank, CS, sm, cl);
+        if (nch > 1) res_final<S>(I, rank, CS, sm, cl);
     }
     if (rank == 0) resid_item(I, idx, tol, resid_all);
 }
