@@ -495,7 +495,7 @@ constexpr int CL_ROWS = 5 + 6 + 15;    // closure item: gradients, scalars, coef
 
 __host__ __device__ inline int nodal_smem_doubles(int qmax) {
     const int r01 = (NOD_WARPS + 1) * 4 * qmax * TILE;
-    const int r2 = (CL_ROWS + 4 * QYMAX + 3 * QZMAX + 8 * QYMAX) * TILE;
+    const int r2 = (CL_ROWS + 4 * QYMAX + 3 * QZMAX + 8 * QYMAX + 2 * MYMAX * (QYMAX + 1)) * TILE;
     return r01 > r2 ? r01 : r2;
 }
 
@@ -619,43 +619,6 @@ __device__ __forceinline__ df r_tab(const double*, const float2* p, int k, df) {
 __device__ __forceinline__ double r_dbl(double x) { return x; }
 __device__ __forceinline__ double r_dbl(df x) { return (double)x.hi + (double)x.lo; }
 
-// Full-range projection row a of (p - u0)^a g on the Qn nodes (App. A): sum over the auxiliary
-// rule (M points) of w (p - u0)^a h_l(p), then the H matrix.  R: arithmetic type.
-template <typename R>
-__device__ void full_row(int a, int Qn, int M, const double* aq, const double* aw, const double* H, const float2* aq2,
-                         const float2* aw2, const float2* H2, const double* fsq, const double* fisq, const float2* fsq2,
-                         const float2* fisq2, R sT, R u0, R* P) {
-    const int lane = threadIdx.x & 31;
-    const R zero = r_of(0.0, R{}), one = r_of(1.0, R{});
-    R G[QYMAX > QZMAX ? QYMAX : QZMAX];
-#pragma unroll
-    for (int l = 0; l < QYMAX; ++l) G[l] = zero;
-    for (int m = 0; m < M; ++m) {
-        const R y = sT * r_tab(aq, aq2, m, R{}), x = u0 + y;
-        R e = r_tab(aw, aw2, m, R{});
-        for (int j = 0; j < a; ++j) e = e * y;
-        R hm = zero, h = one;
-#pragma unroll
-        for (int l = 0; l < QYMAX; ++l) {
-            if (l < Qn) {
-                G[l] = e * h + G[l];
-                const R hn = (x * h - r_tab(fsq, fsq2, l, R{}) * hm) * r_tab(fisq, fisq2, l + 1, R{});
-                hm = h;
-                h = hn;
-            }
-        }
-    }
-    for (int k2 = 0; k2 < QYMAX; ++k2) {
-        if (k2 < Qn) {
-            R t = zero;
-#pragma unroll
-            for (int l = 0; l < QYMAX; ++l)
-                if (l < Qn) t = r_tab(H, H2, l * Qn + k2, R{}) * G[l] + t;
-            P[k2 * TILE + lane] = t;
-        }
-    }
-}
-
 // Output rows of the projection table in the closure's arithmetic type.
 __device__ __forceinline__ double* r_out(const Inst& I, double) { return I.tab; }
 __device__ __forceinline__ float* r_out(const Inst& I, df) { return I.tab32; }
@@ -666,7 +629,8 @@ __device__ __forceinline__ void r_put(float* p, size_t r, df v) { p[r] = df_floa
 // 13 coefficients of f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j) (Eq. j1), the y and z
 // projections (App. A) and the transverse factors n Y[a][t]; wall densities (Sec. III B).
 // Phase A: warps 0..4 one gradient each, warp 5 sqrt T, warp 6 the wall densities, warp 7 the
-// FP64 closure chain; phase B: coefficients and projection rows; phase C: assembly.
+// FP64 closure chain; phase B: coefficients and the recurrence at each auxiliary point, then
+// the projection rows; phase C: assembly.
 template <typename R>
 __device__ void closure_item(const Inst& I, int i0, double* nsm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -680,6 +644,8 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
     R* Py = sc + 15 * TILE;                             // [4 QYMAX][32]
     R* Pz = Py + 4 * QYMAX * TILE;                      // [3 QZMAX][32]
     R* Ay = Pz + 3 * QZMAX * TILE;                      // [8 QYMAX][32]
+    R* hp = Ay + 8 * QYMAX * TILE;                      // [2 MYMAX][QYMAX][32] h_l at the auxiliary points
+    R* yp = hp + 2 * MYMAX * QYMAX * TILE;              // [2 MYMAX][32] p - u0 at the auxiliary points
     if (wid < 5) {
         const int row = wid == 0 ? R_LNN : (wid == 1 ? R_LNCHI : (wid == 2 ? R_LNT : (wid == 3 ? R_UX : R_UY)));
         const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
@@ -760,16 +726,59 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
             case 6: sc[14 * TILE + lane] = r_of(1.0 / tau, z); break;
             default: break;
         }
-        // full-range projections: warps 0..3 rows a = wid of Py (p_y - u_y)^a g, warps 4..6 rows
-        // a = wid - 4 of Pz (p_z^a g)
-        if (I.form != FORM_REDUCED1D && (wid < 4 || (I.form == FORM_UNREDUCED && wid < 7))) {
-            const R sT = r_of(cs[4 * TILE + lane], z);
-            if (wid < 4)
-                full_row<R>(wid, Qy, I.My, I.yq, I.yw, I.yH, I.yq2, I.yw2, I.yH2, I.fsq, I.fisq, I.fsq2, I.fisq2, sT,
-                            r_of(nd[R_UY * ld + ic], z), Py + wid * QYMAX * TILE);
-            else
-                full_row<R>(wid - 4, Qz, I.Mz, I.zq, I.zw, I.zH, I.zq2, I.zw2, I.zH2, I.fsq, I.fisq, I.fsq2, I.fisq2, sT, z,
-                            Pz + (wid - 4) * QZMAX * TILE);
+        // full-range projections, step 1: the orthonormal recurrence h_l at each auxiliary point
+        // (y points first, then z points), one point per warp
+        if (I.form != FORM_REDUCED1D) {
+            const int My = I.My, Mz = I.form == FORM_UNREDUCED ? I.Mz : 0;
+            const R sT = r_of(cs[4 * TILE + lane], z), uy = r_of(nd[R_UY * ld + ic], z), one = r_of(1.0, z);
+            for (int pt = wid; pt < My + Mz; pt += NOD_WARPS) {
+                const bool ydir = pt < My;
+                const int m = ydir ? pt : pt - My, Qn = ydir ? Qy : Qz;
+                const R y = sT * (ydir ? r_tab(I.yq, I.yq2, m, z) : r_tab(I.zq, I.zq2, m, z));
+                const R x = ydir ? uy + y : y;
+                yp[pt * TILE + lane] = y;
+                R hm = z, h = one;
+#pragma unroll
+                for (int l = 0; l < QYMAX; ++l) {
+                    if (l < Qn) {
+                        hp[(pt * QYMAX + l) * TILE + lane] = h;
+                        const R hn = (x * h - r_tab(I.fsq, I.fsq2, l, z) * hm) * r_tab(I.fisq, I.fisq2, l + 1, z);
+                        hm = h;
+                        h = hn;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (I.form != FORM_REDUCED1D && (wid < 4 || (I.form == FORM_UNREDUCED && wid < 7))) {
+        // step 2: warps 0..3 rows a = wid of Py ((p_y - u_y)^a g), warps 4..6 rows a = wid - 4 of
+        // Pz (p_z^a g): sum over the auxiliary points of w y^a h_l, then the H matrix (App. A)
+        const bool ydir = wid < 4;
+        const int a = ydir ? wid : wid - 4, Qn = ydir ? Qy : Qz, M = ydir ? I.My : I.Mz, p0 = ydir ? 0 : I.My;
+        const double* aw = ydir ? I.yw : I.zw;
+        const float2* aw2 = ydir ? I.yw2 : I.zw2;
+        const R z = r_of(0.0, R{});
+        R G[QYMAX];
+#pragma unroll
+        for (int l = 0; l < QYMAX; ++l) G[l] = z;
+        for (int m = 0; m < M; ++m) {
+            const R y = yp[(p0 + m) * TILE + lane];
+            R e = r_tab(aw, aw2, m, z);
+            for (int j = 0; j < a; ++j) e = e * y;
+#pragma unroll
+            for (int l = 0; l < QYMAX; ++l)
+                if (l < Qn) G[l] = e * hp[((p0 + m) * QYMAX + l) * TILE + lane] + G[l];
+        }
+        const double* H = ydir ? I.yH : I.zH;
+        const float2* H2 = ydir ? I.yH2 : I.zH2;
+        R* P = ydir ? Py + a * QYMAX * TILE : Pz + a * QZMAX * TILE;
+        for (int k2 = 0; k2 < Qn; ++k2) {
+            R t = z;
+#pragma unroll
+            for (int l = 0; l < QYMAX; ++l)
+                if (l < Qn) t = r_tab(H, H2, l * Qn + k2, z) * G[l] + t;
+            P[k2 * TILE + lane] = t;
         }
     }
     __syncthreads();
