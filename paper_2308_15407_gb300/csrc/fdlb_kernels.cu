@@ -491,7 +491,7 @@ __device__ void moments_final_tile(const Inst& I, int i0, double* ss, int tid, i
 // role 2 = gradients, closure, coefficients, y and z projections and the transverse factors.
 // Shared doubles: role 0/1: [NOD_WARPS][4Q][32] partials + [4Q][32] sums;
 //                 role 2:   [20][32] scalars + Py [4 QYMAX][32] + Pz [3 QZMAX][32] + A [8 QYMAX][32].
-constexpr int CL_ROWS = 5 + 6 + 15;    // closure item: gradients, scalars, coefficients
+constexpr int CL_ROWS = 5 + 8 + 15;    // closure item: gradients, scalars, coefficients
 
 __host__ __device__ inline int nodal_smem_doubles(int qmax) {
     const int r01 = (NOD_WARPS + 1) * 4 * qmax * TILE;
@@ -639,8 +639,8 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
     const int ic = valid ? i : N - 1;           // padding lanes work on a real node, write nothing
     const double* nd = I.node;
     double* gr = nsm;                           // [5][32] d/dx of ln n, ln chi, ln T, u_x, u_y
-    double* cs = gr + 5 * TILE;                 // [6][32] b rho chi, A, 1/T, mu0c X / (T n), sqrt T, n
-    R* sc = reinterpret_cast<R*>(cs + 6 * TILE);        // [15][32] coefficients, n, 1/tau
+    double* cs = gr + 5 * TILE;                 // [8][32] W = -tau b rho chi, A, 1/T, tau, -, n; sqrt T, u_y as R
+    R* sc = reinterpret_cast<R*>(cs + 8 * TILE);        // [15][32] coefficients, n, 1/tau
     R* Py = sc + 15 * TILE;                             // [4 QYMAX][32]
     R* Pz = Py + 4 * QYMAX * TILE;                      // [3 QZMAX][32]
     R* Ay = Pz + 3 * QZMAX * TILE;                      // [8 QYMAX][32]
@@ -660,7 +660,10 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
         }
         gr[wid * TILE + lane] = g * I.xpinv[ic];
     } else if (wid == 5) {
-        cs[4 * TILE + lane] = sqrt(nd[R_T * ld + ic]);
+        // sqrt T and u_y in the projections' arithmetic, converted once
+        R* cr = reinterpret_cast<R*>(cs + 6 * TILE);
+        cr[lane] = r_of(sqrt(nd[R_T * ld + ic]), R{});
+        cr[TILE + lane] = r_of(nd[R_UY * ld + ic], R{});
     } else if (wid == 6) {
         if (i0 == 0 && lane == 0) {
             // zero net mass flux through each wall (Sec. III B): the outgoing wall-face flux is
@@ -677,60 +680,65 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
         const double eta = I.eta0 * n, chi = chi_cs(eta), br = 4.0 * eta, brc = br * chi;
         const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_mu * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
         const double iT = 1.0 / T, in = 1.0 / n;
-        cs[0 * TILE + lane] = brc;
+        // tau = mu/(n T) = mu0c X sqrt T / (T n), W = -tau b rho chi
+        const double tau = I.mu0c * (1.0 / chi + 0.8 * br + k_mu * br * br * chi) * iT * in * sqrt(T);
+        cs[0 * TILE + lane] = -tau * brc;
         cs[1 * TILE + lane] = (1.0 - Pr) * 0.2 * iT * iT * in;
         cs[2 * TILE + lane] = iT;
-        cs[3 * TILE + lane] = I.mu0c * (1.0 / chi + 0.8 * br + k_mu * br * br * chi) * iT * in;
+        cs[3 * TILE + lane] = tau;
         cs[5 * TILE + lane] = n;
     }
     __syncthreads();
     {
-        // coefficients: tau = mu/(n T) = cs3 sqrt T, W = -tau b rho chi; warp w takes a few
-        const double tau = cs[3 * TILE + lane] * cs[4 * TILE + lane], W = -tau * cs[0 * TILE + lane];
-        const double A = cs[1 * TILE + lane], iT = cs[2 * TILE + lane];
-        const double Gr = 2.0 * gr[0 * TILE + lane] + gr[1 * TILE + lane] + gr[2 * TILE + lane];
-        const double Br = gr[2 * TILE + lane], Ur = gr[3 * TILE + lane], Vr = gr[4 * TILE + lane];
-        const double qx = nd[R_QX * ld + ic], qy = nd[R_QY * ld + ic];
+        // coefficients: warp w computes a few, reading only what they need
         const R z = r_of(0.0, R{});
+        const double* W = cs + 0 * TILE;
+        const double* A = cs + 1 * TILE;
+        const double* iT = cs + 2 * TILE;
         switch (wid) {
             case 0:
-                sc[0 * TILE + lane] = r_of(1.0 - W * Ur, z);
+                sc[0 * TILE + lane] = r_of(1.0 - W[lane] * gr[3 * TILE + lane], z);
                 sc[13 * TILE + lane] = r_of(cs[5 * TILE + lane], z);
                 break;
-            case 1: sc[1 * TILE + lane] = r_of(-5.0 * A * qx + W * (Gr - 1.5 * Br), z); break;
+            case 1: {
+                const double Gr = 2.0 * gr[0 * TILE + lane] + gr[1 * TILE + lane] + gr[2 * TILE + lane];
+                sc[1 * TILE + lane] = r_of(-5.0 * A[lane] * nd[R_QX * ld + ic] + W[lane] * (Gr - 1.5 * gr[2 * TILE + lane]), z);
+                break;
+            }
             case 2:
-                sc[2 * TILE + lane] = r_of(-5.0 * A * qy, z);
-                sc[6 * TILE + lane] = r_of(I.j1_shear ? W * 0.4 * Vr * iT : 0.0, z);
+                sc[2 * TILE + lane] = r_of(-5.0 * A[lane] * nd[R_QY * ld + ic], z);
+                sc[6 * TILE + lane] = I.j1_shear ? r_of(W[lane] * 0.4 * gr[4 * TILE + lane] * iT[lane], z) : z;
                 break;
             case 3: {
-                const double u = W * Ur * iT;
+                const double u = W[lane] * gr[3 * TILE + lane] * iT[lane];
                 sc[3 * TILE + lane] = r_of(0.6 * u, z);
                 sc[4 * TILE + lane] = r_of(0.2 * u, z);
                 sc[5 * TILE + lane] = sc[4 * TILE + lane];
                 break;
             }
             case 4: {
-                const R c3 = r_of(A * qx * iT + W * 0.3 * Br * iT, z);
+                const R c3 = r_of(A[lane] * nd[R_QX * ld + ic] * iT[lane] + W[lane] * 0.3 * gr[2 * TILE + lane] * iT[lane], z);
                 sc[7 * TILE + lane] = c3;
                 sc[8 * TILE + lane] = c3;
                 sc[9 * TILE + lane] = c3;
                 break;
             }
             case 5: {
-                const R cy = r_of(A * qy * iT, z);
+                const R cy = r_of(A[lane] * nd[R_QY * ld + ic] * iT[lane], z);
                 sc[10 * TILE + lane] = cy;
                 sc[11 * TILE + lane] = cy;
                 sc[12 * TILE + lane] = cy;
                 break;
             }
-            case 6: sc[14 * TILE + lane] = r_of(1.0 / tau, z); break;
+            case 6: sc[14 * TILE + lane] = r_of(1.0 / cs[3 * TILE + lane], z); break;
             default: break;
         }
         // full-range projections, step 1: the orthonormal recurrence h_l at each auxiliary point
         // (y points first, then z points), one point per warp
         if (I.form != FORM_REDUCED1D) {
             const int My = I.My, Mz = I.form == FORM_UNREDUCED ? I.Mz : 0;
-            const R sT = r_of(cs[4 * TILE + lane], z), uy = r_of(nd[R_UY * ld + ic], z), one = r_of(1.0, z);
+            const R* cr = reinterpret_cast<const R*>(cs + 6 * TILE);
+            const R sT = cr[lane], uy = cr[TILE + lane], one = r_of(1.0, z);
             for (int pt = wid; pt < My + Mz; pt += NOD_WARPS) {
                 const bool ydir = pt < My;
                 const int m = ydir ? pt : pt - My, Qn = ydir ? Qy : Qz;
