@@ -629,8 +629,9 @@ __device__ __forceinline__ void r_put(float* p, size_t r, df v) { p[r] = df_floa
 // 13 coefficients of f^S + tau J1 = n g(xi) sum_j c_j xi^(a_j, b_j, c_j) (Eq. j1), the y and z
 // projections (App. A) and the transverse factors n Y[a][t]; wall densities (Sec. III B).
 // Phase A: warps 0..4 one gradient each, warp 5 sqrt T, warp 6 the wall densities, warp 7 the
-// FP64 closure chain; phase B: coefficients and the recurrence at each auxiliary point, then
-// the projection rows; phase C: assembly.
+// FP64 closure chain; warps 0..6 then run the projections (the recurrence at each auxiliary
+// point, then the rows) while warp 7 is still busy.  Phase B: the coefficients; phase C:
+// assembly.
 template <typename R>
 __device__ void closure_item(const Inst& I, int i0, double* nsm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -688,6 +689,66 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
         cs[3 * TILE + lane] = tau;
         cs[5 * TILE + lane] = n;
     }
+    // warps 0..6 go on to the projections (they need sqrt T and u_y only) while warp 7 still
+    // runs the closure chain; named barrier 1 synchronises the 7 warps
+    if (wid < NOD_WARPS - 1) {
+        const R z = r_of(0.0, R{});
+        named_sync(1, (NOD_WARPS - 1) * TILE);
+        // full-range projections, step 1: the orthonormal recurrence h_l at each auxiliary point
+        // (y points first, then z points), one point per warp of warps 0..6
+        if (I.form != FORM_REDUCED1D) {
+            const int My = I.My, Mz = I.form == FORM_UNREDUCED ? I.Mz : 0;
+            const R* cr = reinterpret_cast<const R*>(cs + 6 * TILE);
+            const R sT = cr[lane], uy = cr[TILE + lane], one = r_of(1.0, z);
+            for (int pt = wid; pt < My + Mz; pt += NOD_WARPS - 1) {
+                const bool ydir = pt < My;
+                const int m = ydir ? pt : pt - My, Qn = ydir ? Qy : Qz;
+                const R y = sT * (ydir ? r_tab(I.yq, I.yq2, m, z) : r_tab(I.zq, I.zq2, m, z));
+                const R x = ydir ? uy + y : y;
+                yp[pt * TILE + lane] = y;
+                R hm = z, h = one;
+#pragma unroll
+                for (int l = 0; l < QYMAX; ++l) {
+                    if (l < Qn) {
+                        hp[(pt * QYMAX + l) * TILE + lane] = h;
+                        const R hn = (x * h - r_tab(I.fsq, I.fsq2, l, z) * hm) * r_tab(I.fisq, I.fisq2, l + 1, z);
+                        hm = h;
+                        h = hn;
+                    }
+                }
+            }
+        }
+        named_sync(1, (NOD_WARPS - 1) * TILE);
+        if (I.form != FORM_REDUCED1D && (wid < 4 || I.form == FORM_UNREDUCED)) {
+            // step 2: warps 0..3 rows a = wid of Py ((p_y - u_y)^a g), warps 4..6 rows a = wid - 4 of
+            // Pz (p_z^a g): sum over the auxiliary points of w y^a h_l, then the H matrix (App. A)
+            const bool ydir = wid < 4;
+            const int a = ydir ? wid : wid - 4, Qn = ydir ? Qy : Qz, M = ydir ? I.My : I.Mz, p0 = ydir ? 0 : I.My;
+            const double* aw = ydir ? I.yw : I.zw;
+            const float2* aw2 = ydir ? I.yw2 : I.zw2;
+            R G[QYMAX];
+#pragma unroll
+            for (int l = 0; l < QYMAX; ++l) G[l] = z;
+            for (int m = 0; m < M; ++m) {
+                const R y = yp[(p0 + m) * TILE + lane];
+                R e = r_tab(aw, aw2, m, z);
+                for (int j = 0; j < a; ++j) e = e * y;
+#pragma unroll
+                for (int l = 0; l < QYMAX; ++l)
+                    if (l < Qn) G[l] = e * hp[((p0 + m) * QYMAX + l) * TILE + lane] + G[l];
+            }
+            const double* H = ydir ? I.yH : I.zH;
+            const float2* H2 = ydir ? I.yH2 : I.zH2;
+            R* P = ydir ? Py + a * QYMAX * TILE : Pz + a * QZMAX * TILE;
+            for (int k2 = 0; k2 < Qn; ++k2) {
+                R t = z;
+#pragma unroll
+                for (int l = 0; l < QYMAX; ++l)
+                    if (l < Qn) t = r_tab(H, H2, l * Qn + k2, z) * G[l] + t;
+                P[k2 * TILE + lane] = t;
+            }
+        }
+    }
     __syncthreads();
     {
         // coefficients: warp w computes a few, reading only what they need
@@ -732,61 +793,6 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
             }
             case 6: sc[14 * TILE + lane] = r_of(1.0 / cs[3 * TILE + lane], z); break;
             default: break;
-        }
-        // full-range projections, step 1: the orthonormal recurrence h_l at each auxiliary point
-        // (y points first, then z points), one point per warp
-        if (I.form != FORM_REDUCED1D) {
-            const int My = I.My, Mz = I.form == FORM_UNREDUCED ? I.Mz : 0;
-            const R* cr = reinterpret_cast<const R*>(cs + 6 * TILE);
-            const R sT = cr[lane], uy = cr[TILE + lane], one = r_of(1.0, z);
-            for (int pt = wid; pt < My + Mz; pt += NOD_WARPS) {
-                const bool ydir = pt < My;
-                const int m = ydir ? pt : pt - My, Qn = ydir ? Qy : Qz;
-                const R y = sT * (ydir ? r_tab(I.yq, I.yq2, m, z) : r_tab(I.zq, I.zq2, m, z));
-                const R x = ydir ? uy + y : y;
-                yp[pt * TILE + lane] = y;
-                R hm = z, h = one;
-#pragma unroll
-                for (int l = 0; l < QYMAX; ++l) {
-                    if (l < Qn) {
-                        hp[(pt * QYMAX + l) * TILE + lane] = h;
-                        const R hn = (x * h - r_tab(I.fsq, I.fsq2, l, z) * hm) * r_tab(I.fisq, I.fisq2, l + 1, z);
-                        hm = h;
-                        h = hn;
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (I.form != FORM_REDUCED1D && (wid < 4 || (I.form == FORM_UNREDUCED && wid < 7))) {
-        // step 2: warps 0..3 rows a = wid of Py ((p_y - u_y)^a g), warps 4..6 rows a = wid - 4 of
-        // Pz (p_z^a g): sum over the auxiliary points of w y^a h_l, then the H matrix (App. A)
-        const bool ydir = wid < 4;
-        const int a = ydir ? wid : wid - 4, Qn = ydir ? Qy : Qz, M = ydir ? I.My : I.Mz, p0 = ydir ? 0 : I.My;
-        const double* aw = ydir ? I.yw : I.zw;
-        const float2* aw2 = ydir ? I.yw2 : I.zw2;
-        const R z = r_of(0.0, R{});
-        R G[QYMAX];
-#pragma unroll
-        for (int l = 0; l < QYMAX; ++l) G[l] = z;
-        for (int m = 0; m < M; ++m) {
-            const R y = yp[(p0 + m) * TILE + lane];
-            R e = r_tab(aw, aw2, m, z);
-            for (int j = 0; j < a; ++j) e = e * y;
-#pragma unroll
-            for (int l = 0; l < QYMAX; ++l)
-                if (l < Qn) G[l] = e * hp[((p0 + m) * QYMAX + l) * TILE + lane] + G[l];
-        }
-        const double* H = ydir ? I.yH : I.zH;
-        const float2* H2 = ydir ? I.yH2 : I.zH2;
-        R* P = ydir ? Py + a * QYMAX * TILE : Pz + a * QZMAX * TILE;
-        for (int k2 = 0; k2 < Qn; ++k2) {
-            R t = z;
-#pragma unroll
-            for (int l = 0; l < QYMAX; ++l)
-                if (l < Qn) t = r_tab(H, H2, l * Qn + k2, z) * G[l] + t;
-            P[k2 * TILE + lane] = t;
         }
     }
     __syncthreads();
