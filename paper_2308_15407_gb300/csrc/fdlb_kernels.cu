@@ -1,9 +1,6 @@
 // CUDA kernels of the FDLB solver for the simplified Enskog equation (sm_103a).
 //
-// One TVD-RK3 stage (Eq. rk3) is three kernels over a batch of independent channel
-// problems:
-//   k_moments  per node, reduce over all velocities: n, u, T, q, Pi (Eq. macro_LB)
-//              and the outgoing wall-flux partial sums;
+// One TVD-RK3 stage (Eq. rk3) is two kernels over a batch of independent channel problems:
 //   k_nodal    per node: chi (Eq. chi), Pr (Eq. prandtl), tau (Eqs. viscosity, tau),
 //              6th-order gradients (Sec. III B 3), the 13 monomial coefficients of
 //              f^S + tau J1 (Sec. II A, Eq. j1) and their projections onto the
@@ -12,12 +9,18 @@
 //   k_update   per (velocity, node): WENO-5 fluxes (Sec. III B 2) with the
 //              diffuse-reflection closure, the p_y-derivative force (App. A,
 //              Eq. kernel_H), relaxation to the projected target and the RK3
-//              combination.
-// After stage 3, k_moments of the new state and k_resid (per-step residual, status).
+//              combination; its epilogue reduces the new values to the moments
+//              n, u, T, q, Pi of every node (Eq. macro_LB) for the next stage.
+// After stage 3, k_resid (per-step residual, status).  k_moments computes the moments
+// from scratch (creation, new profiles, a loaded state) with the epilogue's arithmetic.
+// k_resident runs whole steps of one instance per thread-block cluster with the same item
+// functions.
 //
-// Storage type S (double | float) holds f; compute type C of the per-velocity work
-// is double for FDLB_FP64 and float for FDLB_FP32_STORAGE.  Moments, gradients,
-// projections and the residual are always double.
+// Storage type S (double | float) holds f; compute type C of the per-velocity work is
+// double for FDLB_FP64 and float for FDLB_FP32_STORAGE.  FP64 instances do all the rest in
+// double; FP32-storage instances run the moment sums and the velocity projections in
+// double-float (float pairs) and keep the closure chain, the moment finalisation and the
+// residual in double.
 #include "fdlb_internal.h"
 #include "fdlb_launch.h"
 #include "../../include/fdlb.h"
