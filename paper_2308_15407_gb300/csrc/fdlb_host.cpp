@@ -48,7 +48,7 @@ struct fdlb_ctx {
     cudaStream_t stream = nullptr;
     size_t smem_upd_f64 = 0, smem_upd_f32 = 0;
     bool any_fp32 = false, any_fp64 = false;
-    int ntab_max = 0, ukc_max = 1;
+    int ukc_max = 1;
     // schedule (FDLB_SCHED_*): requested, and the one in use once chosen (0 = not yet)
     int sched_req = FDLB_SCHED_AUTO, sched = 0;
     int cs = 0;                       // CTAs per cluster of the resident schedule (0: unavailable)
@@ -717,7 +717,6 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             for (int role = 0; role < 3; ++role) wn.push_back({ii, t * TILE, role, 0});
         }
         c->qmax = std::max(c->qmax, Q);
-        c->ntab_max = std::max(c->ntab_max, L.ntab);
         c->ukc_max = std::max(c->ukc_max, L.ukc);
         if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, update_smem_bytes(L.ntab, L.ukc, 8, 8)), c->any_fp64 = true;
         if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, update_smem_bytes(L.ntab, L.ukc, 4, 4)), c->any_fp32 = true;

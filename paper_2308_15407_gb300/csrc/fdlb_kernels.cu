@@ -357,8 +357,8 @@ struct InnerSum<float> {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// Per node: the 14 raw sums over all velocities, factorised as sum_kx px^a (sum_t w_j(t) f).
-constexpr int MOM3_WARPS = 4;
+// Per node: the 14 raw sums over all velocities, factorised as sum_kx px^a (sum_t w_j(t) f),
+// and the moments they give.
 
 // Temperature from the raw sums (the same operations wherever it is needed).
 __device__ __forceinline__ double sums_temperature(double n, double s1, double s2, double s3, double s4, double s6,
