@@ -52,6 +52,12 @@ is used):
       ||T^n||, ||u_x^n - u_x^{n-1}||, ||u_y^n - u_y^{n-1}|| with the cell-width
       weighted L2 norm ||v|| = sqrt(sum_i x'_i ds v_i^2).
   R10 Time step dt = CFL min_i(x'(s_i) ds) / max_k p_k unless given.
+  R15 chi_RET-FM (Eq. chi_ret): chi_SET of the density averaged over a ball of radius
+      sigma = 6 sqrt(2) eta0 chi(eta0) Kn (the Kn definition of Sec. II A with n0 = D = 1),
+      evaluated at the node; b rho in the closure stays the local 4 eta0 n.  In the
+      channel n depends on x only, is constant on each grid cell and zero beyond the
+      walls, which reduces the ball average to a 1D average with weight
+      3 (sigma^2 - t^2)/(4 sigma^3), integrated exactly over each cell.
 """
 from __future__ import annotations
 
@@ -87,6 +93,7 @@ class Params:
     j1_shear: bool = False
     flow: int = FOURIER
     T_init: float = 0.0     # 0 -> mean wall temperature
+    chi_model: str = "set"  # "set": chi_SET[n]; "ret-fm": chi_SET[n-bar] (Eq. chi_ret, R15)
 
 
 # ----------------------------------------------------------------------------
@@ -118,12 +125,31 @@ def mu0(T, kn, eta0):
     return (5.0 / 16.0) * math.sqrt(2.0 * math.pi) * float(chi_set(eta0)) * kn * np.sqrt(T)
 
 
-def viscosity(n, T, kn, eta0):
-    """Enskog shear viscosity, Eq. (viscosity): mu0 [1/chi + 4/5 b rho + 4/25 (1 + 12/pi)(b rho)^2 chi]."""
+def viscosity(n, T, kn, eta0, chi=None):
+    """Enskog shear viscosity, Eq. (viscosity): mu0 [1/chi + 4/5 b rho + 4/25 (1 + 12/pi)(b rho)^2 chi]
+    (chi = chi_SET[n] unless given)."""
     eta = eta0 * np.asarray(n, dtype=np.float64)
-    chi = chi_set(eta)
+    chi = chi_set(eta) if chi is None else chi
     br = 4.0 * eta
     return mu0(T, kn, eta0) * (1.0 / chi + 0.8 * br + (4.0 / 25.0) * (1.0 + 12.0 / math.pi) * br ** 2 * chi)
+
+
+def sphere_diameter(eta0, kn):
+    """Molecular diameter in units of the channel width: Kn = 1/(sqrt(2) pi sigma^2 n0 chi0 D)
+    with b n0 = 4 eta0 and b = 2 pi sigma^3/3 gives sigma = 6 sqrt(2) eta0 chi(eta0) Kn (R1)."""
+    return 6.0 * math.sqrt(2.0) * eta0 * float(chi_set(eta0)) * kn
+
+
+def ret_fm_weights(faces, nodes, sigma):
+    """Averaging matrix of the Fischer-Methfessel density (Eq. chi_ret and the definition of
+    n-bar below it) in a channel, reading R15: n depends on x only and is constant on each
+    cell [faces[j], faces[j+1]], zero outside the walls.  The ball average then reduces to
+    n-bar(x_i) = 3/(4 sigma^3) int n(x_i + t) (sigma^2 - t^2) dt over |t| < sigma, so
+    W[i, j] = 3/(4 sigma^3) int of (sigma^2 - t^2) over the part of cell j within the window."""
+    K = lambda t: sigma * sigma * t - t ** 3 / 3.0
+    lo = np.clip(np.asarray(faces[:-1])[None, :] - np.asarray(nodes)[:, None], -sigma, sigma)
+    hi = np.clip(np.asarray(faces[1:])[None, :] - np.asarray(nodes)[:, None], -sigma, sigma)
+    return 3.0 / (4.0 * sigma ** 3) * (K(hi) - K(lo))
 
 
 def knudsen(eta0, R):
@@ -295,6 +321,13 @@ class Oracle:
         else:
             raise ValueError("grid must be 'uniform' or 'tanh'")
         self.dx = self.xp * self.ds
+        sf = -1.0 + np.arange(N + 1) * self.ds                      # cell faces in s
+        self.faces = 0.5 * sf if prm.grid == "uniform" else 0.5 * np.tanh(prm.stretch * sf) / math.tanh(prm.stretch)
+        if prm.chi_model == "ret-fm":
+            self.sigma = sphere_diameter(prm.eta0, prm.kn)
+            self.Wfm = ret_fm_weights(self.faces, self.x, self.sigma)
+        elif prm.chi_model != "set":
+            raise ValueError("chi_model must be 'set' or 'ret-fm'")
         self.dt = prm.dt if prm.dt > 0 else prm.cfl * self.dx.min() / p.max()
         self.Dmat = gradient_matrix(N)
         self.chi0 = float(chi_set(prm.eta0))
@@ -376,10 +409,10 @@ class Oracle:
         prm = self.prm
         n, T = M["n"], M["T"]
         eta = prm.eta0 * n
-        chi = chi_set(eta)
+        chi = chi_set(prm.eta0 * (self.Wfm @ n)) if prm.chi_model == "ret-fm" else chi_set(eta)
         brc = 4.0 * eta * chi
         Pr = prandtl(brc)
-        tau = viscosity(n, T, prm.kn, prm.eta0) / (n * T)
+        tau = viscosity(n, T, prm.kn, prm.eta0, chi) / (n * T)
         d = lambda q: (self.Dmat @ q) / (self.xp * self.ds)
         G = 2.0 * d(np.log(n)) + d(np.log(chi)) + d(np.log(T))
         B = d(np.log(T))
