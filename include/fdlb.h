@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define FDLB_ABI_VERSION 3
+#define FDLB_ABI_VERSION 4
 
 /* Return codes. */
 #define FDLB_OK            0
@@ -80,6 +80,20 @@ extern "C" {
 #define FDLB_STAGNATION_WINDOW 2000
 #define FDLB_STAGNATION_FACTOR 0.9
 
+/* Contact value of the pair correlation function (Sec. II A).
+ *   FDLB_CHI_SET:    chi_SET of the local density, Eq. (chi) (Carnahan-Starling).
+ *   FDLB_CHI_RET_FM: the Fischer-Methfessel prescription, Eq. (chi_ret): chi_SET of the density
+ *                    averaged over a ball of radius sigma, sigma = 6 sqrt(2) eta0 chi(eta0) Kn
+ *                    in units of the channel width (the Kn definition of Sec. II A with n0 = 1).
+ *                    The density depends on x only, is taken constant on each grid cell and zero
+ *                    beyond the walls; the ball average is then a 1D average with weight
+ *                    3 (sigma^2 - t^2)/(4 sigma^3), integrated exactly over each cell.  b rho in
+ *                    the closure stays local.  Needs eta0 > 0.  It is what produces the density
+ *                    layering next to the walls; with the channel-width units above sigma exceeds
+ *                    the channel for large eta0 Kn, so it is meant for small sigma. */
+#define FDLB_CHI_SET     0
+#define FDLB_CHI_RET_FM  1
+
 /* Per-instance status (fdlb_status). */
 #define FDLB_ACTIVE        0
 #define FDLB_CONVERGED     1
@@ -99,7 +113,7 @@ typedef struct fdlb_params {
     int32_t  qz;          /* full-range order on z, 0 or 3..8; 0 = (phi, theta) reduced slots */
     int32_t  precision;   /* FDLB_FP64 | FDLB_FP32_STORAGE | FDLB_FP32_THEN_FP64 */
     int32_t  j1_shear;    /* 0: J1 as printed for 2D flows; 1: add the 2 zeta_x zeta_y d_x u_y term of Eq. (j1) */
-    int32_t  reserved;    /* must be 0 */
+    int32_t  chi_model;   /* FDLB_CHI_SET | FDLB_CHI_RET_FM */
     double   stretch;     /* A of FDLB_GRID_TANH (> 0) */
     double   kn;          /* Knudsen number referred to the channel width (> 0) */
     double   eta0;        /* mean reduced density eta0 = b n0/4, 0 <= eta0 < 0.5 */

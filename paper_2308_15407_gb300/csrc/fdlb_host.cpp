@@ -324,7 +324,8 @@ int validate(const fdlb_params& p, std::string& why) {
     if (p.precision != FDLB_FP64 && p.precision != FDLB_FP32_STORAGE && p.precision != FDLB_FP32_THEN_FP64)
         return bad("unknown precision");
     if (p.j1_shear != 0 && p.j1_shear != 1) return bad("j1_shear must be 0 or 1");
-    if (p.reserved != 0) return bad("reserved must be 0");
+    if (p.chi_model != FDLB_CHI_SET && p.chi_model != FDLB_CHI_RET_FM) return bad("unknown chi_model");
+    if (p.chi_model == FDLB_CHI_RET_FM && !(p.eta0 > 0)) return bad("chi_model RET-FM needs eta0 > 0");
     if (!(p.kn > 0) || !std::isfinite(p.kn)) return bad("kn must be > 0");
     if (!(p.eta0 >= 0 && p.eta0 < 0.5)) return bad("eta0 must be in [0, 0.5)");
     if (!(p.T_left > 0) || !(p.T_right > 0)) return bad("wall temperatures must be > 0");
@@ -334,10 +335,43 @@ int validate(const fdlb_params& p, std::string& why) {
     return FDLB_OK;
 }
 
+// Fischer-Methfessel averaging weights (Eq. chi_ret) as sparse rows: n-bar_i = sum_e w[e]
+// n[col[e]].  The density is constant on each cell [x(s_j), x(s_{j+1})] and zero beyond the
+// walls; w = 3/(4 sigma^3) times the exact integral of sigma^2 - t^2 over the cell's part of
+// |t| < sigma around x_i, sigma = 6 sqrt(2) eta0 chi(eta0) Kn.
+void fm_weights(const fdlb_params& p, std::vector<int>& ptr, std::vector<int>& col, std::vector<double>& w) {
+    const int N = p.nx;
+    const double ds = 2.0 / N;
+    auto xmap = [&](double s) {
+        return p.grid == FDLB_GRID_UNIFORM ? 0.5 * s : 0.5 * std::tanh(p.stretch * s) / std::tanh(p.stretch);
+    };
+    std::vector<double> faces(N + 1);
+    for (int j = 0; j <= N; ++j) faces[j] = xmap(-1.0 + j * ds);
+    const double eta = p.eta0, chi0 = (2.0 - eta) / (2.0 * (1.0 - eta) * (1.0 - eta) * (1.0 - eta));
+    const double sg = 6.0 * std::sqrt(2.0) * eta * chi0 * p.kn;
+    const double c = 3.0 / (4.0 * sg * sg * sg);
+    auto K = [&](double t) { return sg * sg * t - t * t * t / 3.0; };
+    ptr.assign(1, 0);
+    col.clear();
+    w.clear();
+    for (int i = 0; i < N; ++i) {
+        const double xi = xmap(-1.0 + (i + 0.5) * ds);
+        for (int j = 0; j < N; ++j) {
+            const double lo = std::min(std::max(faces[j] - xi, -sg), sg), hi = std::min(std::max(faces[j + 1] - xi, -sg), sg);
+            if (hi > lo) {
+                col.push_back(j);
+                w.push_back(c * (K(hi) - K(lo)));
+            }
+        }
+        ptr.push_back((int)col.size());
+    }
+}
+
 // Byte layout of one instance inside the workspace.
 struct Layout {
     size_t tables = 0, fbuf = 0, node = 0, tab = 0, tab32 = 0, misc = 0, msum = 0, mcnt = 0, total = 0;
     int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0, groups = 1, ukc = 1;
+    int fm_nnz = 0;            // entries of the Fischer-Methfessel weights (RET-FM only)
 };
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -384,6 +418,13 @@ Layout layout_of(const fdlb_params& p, int ukc) {
         add32(2 * (Q + 1)); add32(2 * Q * Q); add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QYMAX * QYMAX);
         add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QZMAX * QZMAX); add32(2 * (QYMAX + 2)); add32(2 * (QYMAX + 2));
         add32(2 * 2 * Q);   // px pairs
+    }
+    if (p.chi_model == FDLB_CHI_RET_FM) {
+        std::vector<int> pt, cl;
+        std::vector<double> ww;
+        fm_weights(p, pt, cl, ww);
+        L.fm_nnz = (int)cl.size();
+        add32(p.nx + 1); add32(L.fm_nnz); add(L.fm_nnz);
     }
     L.tables = nd * 8;
     const size_t es = p.precision == FDLB_FP32_STORAGE ? 4 : 8;
@@ -486,7 +527,8 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         I.Mx = MX; I.My = L.My; I.Mz = L.Mz;
         I.precision = p.precision == FDLB_FP64 ? FDLB_FP64 : FDLB_FP32_STORAGE;
         I.two_phase = p.precision == FDLB_FP32_THEN_FP64;
-        I.j1_shear = p.j1_shear; I.ntab = L.ntab; I.mgroups = L.groups; I.ukc = L.ukc;
+        I.j1_shear = p.j1_shear;
+        I.chi_model = p.chi_model; I.ntab = L.ntab; I.mgroups = L.groups; I.ukc = L.ukc;
         I.kn = p.kn; I.eta0 = p.eta0; I.chi0 = chi_cs(p.eta0);
         I.mu0c = (5.0 / 16.0) * std::sqrt(2.0 * M_PI) * I.chi0 * p.kn;
         I.accel_y = p.accel_y;
@@ -689,6 +731,17 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             pairs(&I.px2, I.px, 2 * Q);
             const float h0 = (float)I.x_h0;
             I.x_h02 = make_float2(h0, (float)(I.x_h0 - (double)h0));
+        }
+        if (p.chi_model == FDLB_CHI_RET_FM) {
+            std::vector<int> pt, cl;
+            std::vector<double> ww;
+            fm_weights(p, pt, cl, ww);
+            float* hp = put32(reinterpret_cast<const float**>(&I.fm_ptr), pt.size());
+            std::memcpy(hp, pt.data(), sizeof(int) * pt.size());
+            float* hc = put32(reinterpret_cast<const float**>(&I.fm_col), cl.size());
+            std::memcpy(hc, cl.data(), sizeof(int) * cl.size());
+            double* hw = put(&I.fm_w, ww.size());
+            std::memcpy(hw, ww.data(), sizeof(double) * ww.size());
         }
         if (pos * 8 != L.tables) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: table layout mismatch"); }
         regions.push_back({tab_off, L.tables});

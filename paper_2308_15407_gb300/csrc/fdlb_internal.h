@@ -43,6 +43,7 @@ struct Inst {
     int precision;             // storage in use now: FDLB_FP64 or FDLB_FP32_STORAGE (changes once
                                // on the device for two-phase instances)
     int j1_shear;
+    int chi_model;             // FDLB_CHI_SET | FDLB_CHI_RET_FM
     int two_phase;             // FDLB_FP32_THEN_FP64: tables and buffers exist for both storages
     int ntab;                  // doubles per node in the projection table
     int ukc;                   // velocities per update block (chunk) of a tile
@@ -108,6 +109,10 @@ struct Inst {
     const float2* fsq2;
     const float2* fisq2;
     const float2* px2;         // [2Q] x-velocities
+    // Fischer-Methfessel averaging n-bar_i = sum_e w[e] n[col[e]], e in [ptr[i], ptr[i+1]) (RET-FM only)
+    const int* fm_ptr;         // [N+1]
+    const int* fm_col;         // [nnz]
+    const double* fm_w;        // [nnz]
     float2 x_h02;
     void* f[3];                // RK buffers F, A, B; each K*ld elements of the storage type
     double* node;              // [NROWS*ld]

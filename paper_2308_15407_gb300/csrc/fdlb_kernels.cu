@@ -650,6 +650,29 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
     R* Ay = Pz + 3 * QZMAX * TILE;                      // [8 QYMAX][32]
     R* hp = Ay + 8 * QYMAX * TILE;                      // [2 MYMAX][QYMAX][32] h_l at the auxiliary points
     R* yp = hp + 2 * MYMAX * QYMAX * TILE;              // [2 MYMAX][32] p - u0 at the auxiliary points
+    // Fischer-Methfessel contact value (Eq. chi_ret): the averaged density n-bar and ln chi(n-bar)
+    // on the tile and a halo of 7 nodes each side (what the gradient stencils reach)
+    constexpr int FH = 7;
+    __shared__ double fm_nbar[TILE + 2 * FH], fm_lnchi[TILE + 2 * FH];
+    const bool fm = I.chi_model == FDLB_CHI_RET_FM;
+    const int h0 = i0 - FH;
+    if (fm) {
+        for (int h = wid; h < TILE + 2 * FH; h += NOD_WARPS) {
+            const int j = h0 + h;
+            double v = 0.0;
+            if (j >= 0 && j < N)
+                for (int e = I.fm_ptr[j] + lane; e < I.fm_ptr[j + 1]; e += 32) v = fma(I.fm_w[e], nd[R_N * ld + I.fm_col[e]], v);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) fm_nbar[h] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < TILE + 2 * FH) {
+            const int j = h0 + threadIdx.x;
+            fm_lnchi[threadIdx.x] = (j >= 0 && j < N) ? log(chi_cs(I.eta0 * fm_nbar[threadIdx.x])) : 0.0;
+        }
+        __syncthreads();
+    }
     if (wid < 5) {
         const int row = wid == 0 ? R_LNN : (wid == 1 ? R_LNCHI : (wid == 2 ? R_LNT : (wid == 3 ? R_UX : R_UY)));
         const double cen[7] = {-1.0 / 60.0, 3.0 / 20.0, -0.75, 0.0, 0.75, -3.0 / 20.0, 1.0 / 60.0};
@@ -660,7 +683,7 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
             if (ic < 3) { idx = j; wj = I.gst[ic * 7 + j]; }
             else if (ic > N - 4) { const int m = N - 1 - ic; idx = N - 1 - j; wj = -I.gst[m * 7 + j]; }
             else { idx = ic - 3 + j; wj = cen[j]; }
-            g = fma(wj, nd[row * ld + idx], g);
+            g = fma(wj, (fm && wid == 1) ? fm_lnchi[idx - h0] : nd[row * ld + idx], g);
         }
         gr[wid * TILE + lane] = g * I.xpinv[ic];
     } else if (wid == 5) {
@@ -681,7 +704,7 @@ __device__ void closure_item(const Inst& I, int i0, double* nsm) {
         const double k_mu = (4.0 / 25.0) * (1.0 + 12.0 / CUDART_PI);
         const double k_pd = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * CUDART_PI));
         const double n = nd[R_N * ld + ic], T = nd[R_T * ld + ic];
-        const double eta = I.eta0 * n, chi = chi_cs(eta), br = 4.0 * eta, brc = br * chi;
+        const double eta = I.eta0 * n, chi = chi_cs(fm ? I.eta0 * fm_nbar[ic - h0] : eta), br = 4.0 * eta, brc = br * chi;
         const double Pr = (2.0 / 3.0) * (1.0 + 0.8 * brc + k_mu * brc * brc) / (1.0 + 1.2 * brc + k_pd * brc * brc);
         const double iT = 1.0 / T, in = 1.0 / n;
         // tau = mu/(n T) = mu0c X sqrt T / (T n), W = -tau b rho chi

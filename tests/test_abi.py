@@ -59,6 +59,21 @@ def test_parameter_validation(F):
     assert b"struct_size" in lib.fdlb_last_error(None)
 
 
+def test_chi_model_validation(F):
+    """RET-FM instances carry their averaging weights; unknown models and eta0 = 0 are rejected."""
+    base = dict(nx=64, qx_half=4, qy=0, qz=0, kn=0.05, eta0=0.1)
+    b_set = F.workspace_bytes([F.Params(**base)])
+    b_fm = F.workspace_bytes([F.Params(**base, chi_model="ret-fm")])
+    assert b_fm > b_set
+    lib = F.load()
+    c = F.Params(**base).to_c()
+    c.chi_model = 2
+    assert lib.fdlb_workspace_bytes((F.CParams * 1)(c), 1) == 0
+    assert b"chi_model" in lib.fdlb_last_error(None)
+    with pytest.raises(F.FdlbError):
+        F.workspace_bytes([F.Params(**{**base, "eta0": 0.0}, chi_model="ret-fm")])
+
+
 def test_two_phase_precision_workspace(F):
     """FP32-then-FP64 instances hold f at its FP64 size; unknown precisions are rejected."""
     base = dict(nx=64, qx_half=4, qy=4, qz=4, kn=0.1, eta0=0.1)
