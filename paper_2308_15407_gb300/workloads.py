@@ -65,3 +65,16 @@ def couette_family(count, seed, nx=200, qx_half=6, qy=6, qz=4, grid="tanh", prec
         out.append(dict(nx=nx, qx_half=qx_half, qy=qy, qz=qz, kn=kn, eta0=e, U_left=-u, U_right=u, grid=grid,
                         stretch=1.5, flow=COUETTE, precision=precision))
     return out
+
+
+def paper_geometry(R, eta0, qx_half=8, T_w=1.0, cells_per_sigma=100, precision="fp64"):
+    """The paper's own confinement (Sec. IV): a dense gas at rest between walls L = R sigma
+    apart whose molecule centres reach +-(L - sigma)/2, so the computational width is
+    D = (R - 1) sigma, i.e. sigma = D/(R - 1) in channel-width units; the Kn of Sec. II A,
+    referred to D, is 1/(6 sqrt(2) eta0 chi(eta0) (R - 1)), and Delta x = sigma/100.  The
+    Fischer-Methfessel contact value (Eq. chi_ret) gives the density layering next to the
+    walls.  1D reduced velocity set, walls at rest at temperature T_w."""
+    chi0 = (2.0 - eta0) / (2.0 * (1.0 - eta0) ** 3)
+    kn = 1.0 / (6.0 * np.sqrt(2.0) * eta0 * chi0 * (R - 1.0))
+    return dict(nx=int(round(cells_per_sigma * (R - 1))), qx_half=qx_half, qy=0, qz=0, kn=float(kn), eta0=eta0,
+                T_left=T_w, T_right=T_w, chi_model="ret-fm", precision=precision, flow=0)

@@ -86,3 +86,16 @@ def test_ret_fm_closure_uses_the_average():
     assert C["chi"][0] < ofd.chi_set(0.1 * M["n"][0]) and C["chi"][-1] < ofd.chi_set(0.1 * M["n"][-1])
     o2 = ofd.Oracle(ofd.Params(nx=64, qx_half=4, qy=0, qz=0, kn=0.05, eta0=0.1))
     assert np.allclose(C["chi"][20:44], o2.nodal(M)["chi"][20:44], rtol=1e-14)
+
+
+def test_paper_geometry_parameters():
+    """sigma = D/(R - 1) and Delta x = sigma/100 in the paper's confinement; Kn referred to
+    L = R sigma is the closed form of Sec. II A (1/(6 sqrt(2) eta0 chi0 R))."""
+    from paper_2308_15407_gb300 import workloads
+    for R, eta0 in ((4, 0.1), (10, 0.2), (4, 0.01)):
+        d = workloads.paper_geometry(R, eta0)
+        sigma = ofd.sphere_diameter(eta0, d["kn"])
+        assert abs(sigma * (R - 1) - 1.0) < 1e-13
+        assert abs((1.0 / d["nx"]) / sigma - 0.01) < 1e-12
+        kn_L = d["kn"] * (R - 1) / R
+        assert abs(kn_L - ofd.knudsen(eta0, R)) < 1e-15
