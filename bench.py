@@ -49,6 +49,10 @@ WORKLOAD = "Couette sweep: 12 instances (eta0 {0.1,0.2,0.3,0.4} x Kn {0.05,0.1,0
 # nominal peaks used for ALU-bound kernels (152 SMs x lanes x 2 flops x 2.07 GHz max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12      # 80.5
 FP64_PEAK_TFLOPS = 1.25                                # recipe nominal (measured FMA probe: 1.22)
+# DRAM read + write bytes per k_update<float,float> launch on the 12-instance sweep, mean over
+# the three stages of one ncu capture (profiles/update_dram_couette12.md); reset to None when
+# that kernel changes
+UPDATE_TRAFFIC_BYTES = 6885632
 
 
 def couette_params(F, precision="fp32"):
@@ -325,7 +329,10 @@ def run_fdlb(args):
     achieved = flops_per_launch / avg_launch_s / 1e12
     roofline = {"bound": "alu", "kernel": {"update": "k_update<float,float>", "moments": "k_moments<float>",
                                            "nodal": "k_nodal<8>", "resid": "k_resid"}[dom],
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": UPDATE_TRAFFIC_BYTES if dom == "update" else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache, "
+                                  "profiles/update_dram_couette12.md",
                 "peak_source": ("nominal FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz" if fp32_dom else
                                 "nominal FP64 1.25 TFLOP/s (profiling recipe; FMA probe measured 1.22); achieved counts the "
                                 "algorithm's operations, which FP32-storage instances partly run in double-float on the FP32 pipe"),
