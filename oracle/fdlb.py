@@ -58,6 +58,12 @@ is used):
       channel n depends on x only, is constant on each grid cell and zero beyond the
       walls, which reduces the ball average to a 1D average with weight
       3 (sigma^2 - t^2)/(4 sigma^3), integrated exactly over each cell.
+  R16 Full-range x quadrature (App. A; the comparison of its last figure): the
+      full-range Gauss-Hermite rule of even order 2 Q_x^h replaces the two
+      half-range rules, so the x-velocities keep the form {+p_k} u {-p_k} (an
+      odd order would add a zero node, which this layout does not hold).  The
+      discrete equilibrium is one expansion over the whole axis truncated at
+      order 2 Q_x^h - 1 (Eq. H_gk); walls, fluxes and moments are unchanged.
 """
 from __future__ import annotations
 
@@ -94,6 +100,8 @@ class Params:
     flow: int = FOURIER
     T_init: float = 0.0     # 0 -> mean wall temperature
     chi_model: str = "set"  # "set": chi_SET[n]; "ret-fm": chi_SET[n-bar] (Eq. chi_ret, R15)
+    x_quadrature: str = "half"  # "half": half-range order qx_half per side (Sec. III A 2);
+                                # "full": full-range Gauss-Hermite order 2 qx_half (App. A)
 
 
 # ----------------------------------------------------------------------------
@@ -280,9 +288,17 @@ class Oracle:
         self.N = N
         Q = prm.qx_half
         self.Q = Q
-        # x axis: half-range rule, discrete set {+p_k} then {-p_k} (Eq. hh_pk)
-        self.xrule = qd.half_range_rule(Q)
-        p = self.xrule.nodes
+        # x axis: half-range rule, discrete set {+p_k} then {-p_k} (Eq. hh_pk); or the
+        # full-range rule of even order 2Q (App. A), whose nodes are the same kind of set
+        # {+p_k} u {-p_k} (no zero node), stored in the same order
+        if prm.x_quadrature == "half":
+            self.xrule = qd.half_range_rule(Q)
+            p = self.xrule.nodes
+        elif prm.x_quadrature == "full":
+            self.xrule = qd.full_range_rule(2 * Q)
+            p = self.xrule.nodes[Q:]              # ascending: the positive half
+        else:
+            raise ValueError("x_quadrature must be 'half' or 'full'")
         self.px = np.concatenate([p, -p])
         # transverse axes
         if prm.qy > 0:
@@ -345,6 +361,9 @@ class Oracle:
     # -- velocity-space projections (R2) -----------------------------------
     def x_projection(self, ux, T):
         """P^x[a, kx, i]: projected (p_x - u_x)^a g(p_x; u_x, T) on the 2Q x-velocities."""
+        if self.prm.x_quadrature == "full":
+            # one expansion over the whole axis, truncated at order 2Q - 1 (App. A, Eq. H_gk)
+            return qd.project_full(self.px, ux, T)
         p = self.xrule.nodes
         pos = qd.project_half(p, ux, T)
         neg = qd.project_half(p, -ux, T)
