@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define FDLB_ABI_VERSION 4
+#define FDLB_ABI_VERSION 5
 
 /* Return codes. */
 #define FDLB_OK            0
@@ -94,6 +94,18 @@ extern "C" {
 #define FDLB_CHI_SET     0
 #define FDLB_CHI_RET_FM  1
 
+/* Quadrature on the wall-normal axis x (fdlb_params.x_quadrature).
+ *   FDLB_XQ_HALF: half-range Gauss-Hermite rules of order qx_half on each half-axis
+ *                 (Sec. III A 2); the discrete equilibrium is truncated at order qx_half - 1
+ *                 on each half-axis.
+ *   FDLB_XQ_FULL: one full-range Gauss-Hermite rule of even order 2 qx_half (App. A), the
+ *                 variant the paper compares against; its nodes are +-p_k (no zero node), so
+ *                 the 2 qx_half x-velocities keep their layout.  The discrete equilibrium is
+ *                 the expansion over the whole axis truncated at order 2 qx_half - 1.  Needs
+ *                 qx_half <= 8.  Walls, fluxes and moments are the same as with FDLB_XQ_HALF. */
+#define FDLB_XQ_HALF     0
+#define FDLB_XQ_FULL     1
+
 /* Per-instance status (fdlb_status). */
 #define FDLB_ACTIVE        0
 #define FDLB_CONVERGED     1
@@ -108,12 +120,14 @@ typedef struct fdlb_params {
     int32_t  flow;        /* FDLB_FOURIER | FDLB_COUETTE | FDLB_POISEUILLE */
     int32_t  nx;          /* grid nodes, 8 <= nx <= 4096 */
     int32_t  grid;        /* FDLB_GRID_UNIFORM | FDLB_GRID_TANH */
-    int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..16 (2*qx_half x-velocities) */
+    int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..16 (2*qx_half x-velocities);
+                             with FDLB_XQ_FULL half the full-range order, 1..8 */
     int32_t  qy;          /* full-range order on y, 0 or 2..8; 0 = 1D reduced (p_y integrated out) */
     int32_t  qz;          /* full-range order on z, 0 or 3..8; 0 = (phi, theta) reduced slots */
     int32_t  precision;   /* FDLB_FP64 | FDLB_FP32_STORAGE | FDLB_FP32_THEN_FP64 */
     int32_t  j1_shear;    /* 0: J1 as printed for 2D flows; 1: add the 2 zeta_x zeta_y d_x u_y term of Eq. (j1) */
     int32_t  chi_model;   /* FDLB_CHI_SET | FDLB_CHI_RET_FM */
+    int32_t  x_quadrature;  /* FDLB_XQ_HALF | FDLB_XQ_FULL */
     double   stretch;     /* A of FDLB_GRID_TANH (> 0) */
     double   kn;          /* Knudsen number referred to the channel width (> 0) */
     double   eta0;        /* mean reduced density eta0 = b n0/4, 0 <= eta0 < 0.5 */

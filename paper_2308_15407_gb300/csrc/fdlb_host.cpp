@@ -326,6 +326,9 @@ int validate(const fdlb_params& p, std::string& why) {
     if (p.j1_shear != 0 && p.j1_shear != 1) return bad("j1_shear must be 0 or 1");
     if (p.chi_model != FDLB_CHI_SET && p.chi_model != FDLB_CHI_RET_FM) return bad("unknown chi_model");
     if (p.chi_model == FDLB_CHI_RET_FM && !(p.eta0 > 0)) return bad("chi_model RET-FM needs eta0 > 0");
+    if (p.x_quadrature != FDLB_XQ_HALF && p.x_quadrature != FDLB_XQ_FULL) return bad("unknown x_quadrature");
+    if (p.x_quadrature == FDLB_XQ_FULL && p.qx_half > QMAX / 2)
+        return bad("the full-range x quadrature needs qx_half <= 8 (order 2 qx_half <= 16)");
     if (!(p.kn > 0) || !std::isfinite(p.kn)) return bad("kn must be > 0");
     if (!(p.eta0 >= 0 && p.eta0 < 0.5)) return bad("eta0 must be in [0, 0.5)");
     if (!(p.T_left > 0) || !(p.T_right > 0)) return bad("wall temperatures must be > 0");
@@ -396,11 +399,11 @@ Layout layout_of(const fdlb_params& p, int ukc) {
     L.ntab = 8 * p.qx_half + 4 * L.Tc + 1;
     L.My = p.qy > 0 ? (p.qy + 5) / 2 : 0;     // 2 My - 1 >= qy + 2
     L.Mz = p.qz > 0 ? (p.qz + 5) / 2 : 0;
-    const int Q = p.qx_half;
+    const int Q = p.qx_half, Lx = p.x_quadrature == FDLB_XQ_FULL ? 2 * Q : Q;
     size_t nd = 0;
     // tables (doubles), each padded to 256 B
     auto add = [&](size_t n) { nd += al256(n * 8) / 8; };
-    add(2 * Q); add(MX); add(MX); add(MX8); add(MX8); add(Q); add(Q + 1); add(Q + 1); add(Q * Q);
+    add(2 * Q); add(MX); add(MX); add(MX8); add(MX8); add(Lx); add(Lx + 1); add(Lx + 1); add(Lx * Q);
     add(QYMAX); add(MYMAX); add(MYMAX); add(QYMAX * QYMAX);
     add(QZMAX); add(MYMAX); add(MYMAX); add(QZMAX * QZMAX);
     add(QYMAX * QYMAX);
@@ -414,8 +417,8 @@ Layout layout_of(const fdlb_params& p, int ukc) {
     if (f32) {
         add32(2 * Q); add32(p.nx); add32(QYMAX * QYMAX); add32(L.K); add32(L.K);
         // float pairs: xq, xw, xq8, xw8, xa, xb, xib, xH, yq, yw, yH, zq, zw, zH, fsq, fisq
-        add32(2 * MX); add32(2 * MX); add32(2 * MX8); add32(2 * MX8); add32(2 * Q); add32(2 * (Q + 1));
-        add32(2 * (Q + 1)); add32(2 * Q * Q); add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QYMAX * QYMAX);
+        add32(2 * MX); add32(2 * MX); add32(2 * MX8); add32(2 * MX8); add32(2 * Lx); add32(2 * (Lx + 1));
+        add32(2 * (Lx + 1)); add32(2 * Lx * Q); add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QYMAX * QYMAX);
         add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QZMAX * QZMAX); add32(2 * (QYMAX + 2)); add32(2 * (QYMAX + 2));
         add32(2 * 2 * Q);   // px pairs
     }
@@ -529,6 +532,12 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         I.two_phase = p.precision == FDLB_FP32_THEN_FP64;
         I.j1_shear = p.j1_shear;
         I.chi_model = p.chi_model; I.ntab = L.ntab; I.mgroups = L.groups; I.ukc = L.ukc;
+        const bool xfull = p.x_quadrature == FDLB_XQ_FULL;
+        const int Lx = xfull ? 2 * Q : Q;
+        I.xfull = xfull; I.Lx = Lx;
+        // full range: (p - u)^a h_l(p) g is a polynomial of degree <= Lx + 2 in the Gaussian
+        // variable, integrated exactly by the Gauss-Hermite rule of Q + 2 points
+        if (xfull) I.Mx = Q + 2;
         I.kn = p.kn; I.eta0 = p.eta0; I.chi0 = chi_cs(p.eta0);
         I.mu0c = (5.0 / 16.0) * std::sqrt(2.0 * M_PI) * I.chi0 * p.kn;
         I.accel_y = p.accel_y;
@@ -558,29 +567,32 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             pos += al256(n * 8) / 8;
             return h;
         };
-        Rule xr = make_rule(0, Q);
-        Rule xa = make_rule(0, MX);
+        // x axis: the half-range rule of order Q, or the full-range rule of order 2Q whose
+        // positive nodes (the upper half of its ascending list) play the same part
+        Rule xr = xfull ? make_rule(1, Lx) : make_rule(0, Q);
+        const int kpos = xfull ? Q : 0;            // index of +p_1 in xr.x
+        Rule xa = xfull ? make_rule(1, I.Mx) : make_rule(0, MX);
         {
             double* h = put(&I.px, 2 * Q);
-            for (int k = 0; k < Q; ++k) { h[k] = xr.x[k]; h[Q + k] = -xr.x[k]; }
-            h = put(&I.xq, MX); for (int m = 0; m < MX; ++m) h[m] = xa.x[m];
-            h = put(&I.xw, MX); for (int m = 0; m < MX; ++m) h[m] = xa.w[m];
+            for (int k = 0; k < Q; ++k) { h[k] = xr.x[kpos + k]; h[Q + k] = -xr.x[kpos + k]; }
+            h = put(&I.xq, MX); for (int m = 0; m < I.Mx; ++m) h[m] = xa.x[m];
+            h = put(&I.xw, MX); for (int m = 0; m < I.Mx; ++m) h[m] = xa.w[m];
             Rule xa8 = make_rule(0, MX8);
             h = put(&I.xq8, MX8); for (int m = 0; m < MX8; ++m) h[m] = xa8.x[m];
             h = put(&I.xw8, MX8); for (int m = 0; m < MX8; ++m) h[m] = xa8.w[m];
-            h = put(&I.xa, Q); for (int l = 0; l < Q; ++l) h[l] = xr.alpha[l];
-            double* hb = put(&I.xb, Q + 1);
-            double* hib = put(&I.xib, Q + 1);
-            for (int l = 0; l <= Q; ++l) {
+            h = put(&I.xa, Lx); for (int l = 0; l < Lx; ++l) h[l] = xr.alpha[l];
+            double* hb = put(&I.xb, Lx + 1);
+            double* hib = put(&I.xib, Lx + 1);
+            for (int l = 0; l <= Lx; ++l) {
                 hb[l] = l ? std::sqrt(xr.beta[l]) : 0.0;
                 hib[l] = l ? 1.0 / std::sqrt(xr.beta[l]) : 0.0;
             }
             I.x_h0 = 1.0 / std::sqrt(xr.beta[0]);
-            h = put(&I.xH, Q * Q);
+            h = put(&I.xH, Lx * Q);
             std::vector<double> hv;
             for (int k = 0; k < Q; ++k) {
-                ortho_values(Q, xr.alpha, xr.beta, xr.x[k], hv);
-                for (int l = 0; l < Q; ++l) h[l * Q + k] = (double)(xr.w[k] * hv[l]);
+                ortho_values(Lx, xr.alpha, xr.beta, xr.x[kpos + k], hv);
+                for (int l = 0; l < Lx; ++l) h[l * Q + k] = (double)(xr.w[kpos + k] * hv[l]);
             }
         }
         auto full_tables = [&](int Qn, int M, const double** nn, const double** aq, const double** aw, const double** H) {
@@ -658,7 +670,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
                 hdx[i] = xp * I.ds;
                 xpmin = std::min(xpmin, xp);
             }
-            I.dt = p.dt > 0 ? p.dt : p.cfl * xpmin * I.ds / xr.x[Q - 1];
+            I.dt = p.dt > 0 ? p.dt : p.cfl * xpmin * I.ds / xr.x[kpos + Q - 1];
             double* hg = put(&I.gst, 21);
             for (int r = 0; r < 3; ++r) stencil7(r, hg + 7 * r);
         }
@@ -716,10 +728,10 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             pairs(&I.xw2, I.xw, MX);
             pairs(&I.xq82, I.xq8, MX8);
             pairs(&I.xw82, I.xw8, MX8);
-            pairs(&I.xa2, I.xa, Q);
-            pairs(&I.xb2, I.xb, Q + 1);
-            pairs(&I.xib2, I.xib, Q + 1);
-            pairs(&I.xH2, I.xH, (size_t)Q * Q);
+            pairs(&I.xa2, I.xa, Lx);
+            pairs(&I.xb2, I.xb, Lx + 1);
+            pairs(&I.xib2, I.xib, Lx + 1);
+            pairs(&I.xH2, I.xH, (size_t)Lx * Q);
             pairs(&I.yq2, I.yq, MYMAX);
             pairs(&I.yw2, I.yw, MYMAX);
             pairs(&I.yH2, I.yH, QYMAX * QYMAX);
@@ -769,7 +781,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
             for (int k0 = 0; k0 < L.K; k0 += L.ukc) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + L.ukc)});
             for (int role = 0; role < 3; ++role) wn.push_back({ii, t * TILE, role, 0});
         }
-        c->qmax = std::max(c->qmax, Q);
+        c->qmax = std::max(c->qmax, Lx);      // register and shared arrays hold Lx polynomials
         c->ukc_max = std::max(c->ukc_max, L.ukc);
         if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, update_smem_bytes(L.ntab, L.ukc, 8, 8)), c->any_fp64 = true;
         if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, update_smem_bytes(L.ntab, L.ukc, 4, 4)), c->any_fp32 = true;

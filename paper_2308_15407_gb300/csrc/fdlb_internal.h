@@ -44,23 +44,26 @@ struct Inst {
                                // on the device for two-phase instances)
     int j1_shear;
     int chi_model;             // FDLB_CHI_SET | FDLB_CHI_RET_FM
+    int xfull;                 // x axis: 0 = half-range rules of order Q per side, 1 = one full-range
+                               // rule of order 2Q (App. A)
+    int Lx;                    // orthonormal x polynomials in the projection: Q (half), 2Q (full)
     int two_phase;             // FDLB_FP32_THEN_FP64: tables and buffers exist for both storages
     int ntab;                  // doubles per node in the projection table
     int ukc;                   // velocities per update block (chunk) of a tile
     int mgroups;               // update chunks per tile (> 1: partial moment sums in msum)
     double kn, eta0, chi0, mu0c, dt, ds, accel_y;
     double T_L, T_R, U_L, U_R, T_init;
-    double x_h0;               // h_0 of the half-range orthonormal family
+    double x_h0;               // h_0 of the x axis' orthonormal family
     // tables
     const double* px;          // [2Q]: +p_1..+p_Q, -p_1..-p_Q
-    const double* xq;          // [Mx] aux half-range nodes
-    const double* xw;          // [Mx] aux half-range weights
+    const double* xq;          // [Mx] aux nodes: half-range rule (half), Gauss-Hermite rule (full)
+    const double* xw;          // [Mx] aux weights
     const double* xq8;         // [MX8] 8-point aux half-range nodes
     const double* xw8;         // [MX8] 8-point aux half-range weights
-    const double* xa;          // [Q]   recurrence alpha_l
-    const double* xb;          // [Q+1] recurrence b_l = sqrt(beta_l), b_0 = 0
-    const double* xib;         // [Q+1] 1/b_l (l >= 1)
-    const double* xH;          // [Q*Q] w_k h_l(p_k), index l*Q + k
+    const double* xa;          // [Lx]   recurrence alpha_l
+    const double* xb;          // [Lx+1] recurrence b_l = sqrt(beta_l), b_0 = 0
+    const double* xib;         // [Lx+1] 1/b_l (l >= 1)
+    const double* xH;          // [Lx*Q] w_k h_l(p_k) at the positive nodes, index l*Q + k
     const double* yn;          // [Qy] nodes
     const double* yq;          // [My] aux full-range nodes
     const double* yw;          // [My] aux full-range weights

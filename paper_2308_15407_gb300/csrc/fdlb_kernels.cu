@@ -51,21 +51,28 @@ __device__ __forceinline__ double chi_cs(double eta) {
 // the orthonormal basis, value_k = w_k sum_l h_l(p_k) G_l, with
 //   G_l = int_0^inf h_l(p) (p - u)^a g dp = sum_m W_m exp(q_m v - v^2/2) h_l(sqrt(T) q_m) y_m^a,
 // p = sqrt(T) q, v = u/sqrt(T), y_m = sqrt(T) q_m - u, on the MX-point auxiliary rule.
+// Full-range x axis (App. A, I.xfull): the integrals run over the whole line with the
+// 2Q-node basis, G_l = sum_m W_m h_l(u + sqrt(T) y_m) (sqrt(T) y_m)^a on the Mx-point
+// Gauss-Hermite rule (exact); the rule is symmetric, so the mirror relation for -p_k holds
+// as well.
 __device__ void proj_x(const Inst& I, double u, double T, int half, double* out, int stride) {
-    const int Q = I.Q;
+    const int Q = I.Q, Lx = I.Lx;
+    const bool full = I.xfull;
     double G[4][QMAX];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
         for (int l = 0; l < QMAX; ++l) G[a][l] = 0.0;
     const double uu = half ? -u : u;
     const double sT = sqrt(T), v = uu / sT, ev = -0.5 * v * v;
-    for (int m = 0; m < MX; ++m) {
-        const double q = I.xq[m], x = sT * q;
-        const double E = I.xw[m] * exp(fma(q, v, ev));
-        const double y = x - uu;
+    const int M = full ? I.Mx : MX;
+    for (int m = 0; m < M; ++m) {
+        const double q = I.xq[m];
+        const double x = full ? fma(sT, q, uu) : sT * q;
+        const double E = full ? I.xw[m] : I.xw[m] * exp(fma(q, v, ev));
+        const double y = full ? sT * q : x - uu;
         const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
         double hm = 0.0, h = I.x_h0;
-        for (int l = 0; l < Q; ++l) {
+        for (int l = 0; l < Lx; ++l) {
             G[0][l] = fma(E, h, G[0][l]);
             G[1][l] = fma(e1, h, G[1][l]);
             G[2][l] = fma(e2, h, G[2][l]);
@@ -79,7 +86,7 @@ __device__ void proj_x(const Inst& I, double u, double T, int half, double* out,
         const double sgn = (half && (a & 1)) ? -1.0 : 1.0;
         for (int k = 0; k < Q; ++k) {
             double s = 0.0;
-            for (int l = 0; l < Q; ++l) s = fma(I.xH[l * Q + k], G[a][l], s);
+            for (int l = 0; l < Lx; ++l) s = fma(I.xH[l * Q + k], G[a][l], s);
             out[(a * 2 * Q + half * Q + k) * stride] = sgn * s;
         }
     }
@@ -490,9 +497,10 @@ __device__ void moments_final_tile(const Inst& I, int i0, double* ss, int tid, i
 // per-node closure and projection tables
 // ---------------------------------------------------------------------------
 // Three independent block roles per 32-node tile (lane = node, so every FP64 instruction runs
-// with full lanes): role 0 / 1 = half-range x projection of the positive / negative half-axis,
-// role 2 = gradients, closure, coefficients, y and z projections and the transverse factors.
-// Shared doubles: role 0/1: [NOD_WARPS][4Q][32] partials + [4Q][32] sums;
+// with full lanes): role 0 / 1 = x projection onto the nodes +p_k / -p_k (half-range rules,
+// or the full-range rule of order 2Q), role 2 = gradients, closure, coefficients, y and z
+// projections and the transverse factors.
+// Shared doubles: role 0/1: [NOD_WARPS][4 Lx][32] partials + [4 Lx][32] sums (Lx = Q or 2Q);
 //                 role 2:   [20][32] scalars + Py [4 QYMAX][32] + Pz [3 QZMAX][32] + A [8 QYMAX][32].
 constexpr int CL_ROWS = 5 + 8 + 15;    // closure item: gradients, scalars, coefficients
 
@@ -553,8 +561,10 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
         if (lane == 0) use_short = av < 0.02f ? 1 : 2;
     }
     __syncthreads();
-    const bool short_rule = use_short == 1 && Q <= 12;
-    const int M = short_rule ? MX8 : MX;
+    const bool full = I.xfull;               // full-range x: as in the FP64 branch
+    const int Lx = I.Lx;
+    const bool short_rule = !full && use_short == 1 && Q <= 12;
+    const int M = full ? I.Mx : (short_rule ? MX8 : MX);
     const df sT = df_of(xs[0][lane]), uu = df_of(xs[1][lane]), v = df_of(xs[2][lane]), hv2 = df_of(xs[3][lane]);
     df G[4][QB];
 #pragma unroll
@@ -565,21 +575,30 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
     for (int m = wid; m < M; m += NOD_WARPS) {
         const df q = df_of(short_rule ? I.xq82[m] : I.xq2[m]);
         const df Wm = df_of(short_rule ? I.xw82[m] : I.xw2[m]);
-        const df z = q * v - hv2;
-        df ez;
-        if (short_rule) {
-            ez = one;
-#pragma unroll
-            for (int j = 12; j >= 1; --j) ez = ez * z * df_of(c_inv2[j]) + one;
+        df x, E, y;
+        if (full) {
+            y = sT * q;
+            x = uu + y;
+            E = Wm;
         } else {
-            ez = df_exp(z);
+            const df z = q * v - hv2;
+            df ez;
+            if (short_rule) {
+                ez = one;
+#pragma unroll
+                for (int j = 12; j >= 1; --j) ez = ez * z * df_of(c_inv2[j]) + one;
+            } else {
+                ez = df_exp(z);
+            }
+            x = sT * q;
+            E = Wm * ez;
+            y = x - uu;
         }
-        const df x = sT * q, E = Wm * ez;
-        const df y = x - uu, e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+        const df e1 = E * y, e2 = e1 * y, e3 = e2 * y;
         df hm = {0.0f, 0.0f}, h = df_of(I.x_h02);
 #pragma unroll
         for (int l = 0; l < QB; ++l) {
-            if (l < Q) {
+            if (l < Lx) {
                 G[0][l] = E * h + G[0][l];
                 G[1][l] = e1 * h + G[1][l];
                 G[2][l] = e2 * h + G[2][l];
@@ -590,24 +609,24 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
             }
         }
     }
-    float2* part = reinterpret_cast<float2*>(nsm);                  // [NOD_WARPS][4Q][32]
-    float2* sum = part + NOD_WARPS * 4 * Q * TILE;                  // [4Q][32]
+    float2* part = reinterpret_cast<float2*>(nsm);                  // [NOD_WARPS][4 Lx][32]
+    float2* sum = part + NOD_WARPS * 4 * Lx * TILE;                 // [4 Lx][32]
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int l = 0; l < QB; ++l)
-            if (l < Q) part[((wid * 4 + a) * Q + l) * TILE + lane] = make_float2(G[a][l].hi, G[a][l].lo);
+            if (l < Lx) part[((wid * 4 + a) * Lx + l) * TILE + lane] = make_float2(G[a][l].hi, G[a][l].lo);
     __syncthreads();
-    for (int r = wid; r < 4 * Q; r += NOD_WARPS) {
+    for (int r = wid; r < 4 * Lx; r += NOD_WARPS) {
         df t = {0.0f, 0.0f};
-        for (int q = 0; q < NOD_WARPS; ++q) t = t + df_of(part[(q * 4 * Q + r) * TILE + lane]);
+        for (int q = 0; q < NOD_WARPS; ++q) t = t + df_of(part[(q * 4 * Lx + r) * TILE + lane]);
         sum[r * TILE + lane] = make_float2(t.hi, t.lo);
     }
     __syncthreads();
     for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
         const int a = o / Q, k = o - a * Q;
         df t = {0.0f, 0.0f};
-        for (int l = 0; l < Q; ++l) t = df_of(I.xH2[l * Q + k]) * df_of(sum[(a * Q + l) * TILE + lane]) + t;
+        for (int l = 0; l < Lx; ++l) t = df_of(I.xH2[l * Q + k]) * df_of(sum[(a * Lx + l) * TILE + lane]) + t;
         if (role && (a & 1)) t = -t;
         if (valid) I.tab32[(size_t)(a * 2 * Q + role * Q + k) * ld + i] = df_float(t);
     }
@@ -922,8 +941,12 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
         }
         __syncthreads();
         const double sT = xs[0][lane], uu = xs[1][lane], v = xs[2][lane];
-        const bool short_rule = use_short == 1 && Q <= 12;
-        const int M = short_rule ? MX8 : MX;
+        // full-range x (App. A): Lx = 2Q polynomials, x = u + sqrt(T) q on the exact Mx-point
+        // Gauss-Hermite rule, no exponential (the Maxwellian is the rule's weight)
+        const bool full = I.xfull;
+        const int Lx = I.Lx;
+        const bool short_rule = !full && use_short == 1 && Q <= 12;
+        const int M = full ? I.Mx : (short_rule ? MX8 : MX);
         double G[4][QB];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -932,21 +955,30 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
         for (int m = wid; m < M; m += NOD_WARPS) {
             const double q = short_rule ? I.xq8[m] : I.xq[m];
             const double Wm = short_rule ? I.xw8[m] : I.xw[m];
-            const double z = fma(q, v, -0.5 * v * v);
-            double ez;
-            if (short_rule) {
-                ez = 1.0;
-#pragma unroll
-                for (int j = 12; j >= 1; --j) ez = fma(ez * z, c_inv[j], 1.0);
+            double x, E, y;
+            if (full) {
+                y = sT * q;
+                x = uu + y;
+                E = Wm;
             } else {
-                ez = exp(z);
+                const double z = fma(q, v, -0.5 * v * v);
+                double ez;
+                if (short_rule) {
+                    ez = 1.0;
+#pragma unroll
+                    for (int j = 12; j >= 1; --j) ez = fma(ez * z, c_inv[j], 1.0);
+                } else {
+                    ez = exp(z);
+                }
+                x = sT * q;
+                E = Wm * ez;
+                y = x - uu;
             }
-            const double x = sT * q, E = Wm * ez;
-            const double y = x - uu, e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+            const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
             double hm = 0.0, h = I.x_h0;
 #pragma unroll
             for (int l = 0; l < QB; ++l) {
-                if (l < Q) {
+                if (l < Lx) {
                     G[0][l] = fma(E, h, G[0][l]);
                     G[1][l] = fma(e1, h, G[1][l]);
                     G[2][l] = fma(e2, h, G[2][l]);
@@ -957,24 +989,24 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
                 }
             }
         }
-        double* part = nsm;                                  // [NOD_WARPS][4Q][32]
-        double* sum = nsm + NOD_WARPS * 4 * Q * TILE;        // [4Q][32]
+        double* part = nsm;                                  // [NOD_WARPS][4 Lx][32]
+        double* sum = nsm + NOD_WARPS * 4 * Lx * TILE;       // [4 Lx][32]
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int l = 0; l < QB; ++l)
-                if (l < Q) part[((wid * 4 + a) * Q + l) * TILE + lane] = G[a][l];
+                if (l < Lx) part[((wid * 4 + a) * Lx + l) * TILE + lane] = G[a][l];
         __syncthreads();
-        for (int r = wid; r < 4 * Q; r += NOD_WARPS) {
+        for (int r = wid; r < 4 * Lx; r += NOD_WARPS) {
             double s = 0.0;
-            for (int q = 0; q < NOD_WARPS; ++q) s += part[(q * 4 * Q + r) * TILE + lane];
+            for (int q = 0; q < NOD_WARPS; ++q) s += part[(q * 4 * Lx + r) * TILE + lane];
             sum[r * TILE + lane] = s;
         }
         __syncthreads();
         for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
             const int a = o / Q, k = o - a * Q;
             double s = 0.0;
-            for (int l = 0; l < Q; ++l) s = fma(I.xH[l * Q + k], sum[(a * Q + l) * TILE + lane], s);
+            for (int l = 0; l < Lx; ++l) s = fma(I.xH[l * Q + k], sum[(a * Lx + l) * TILE + lane], s);
             if (role && (a & 1)) s = -s;
             if (valid) {
                 const size_t r = (size_t)(a * 2 * Q + role * Q + k) * ld + i;

@@ -19,6 +19,7 @@ FOURIER, COUETTE, POISEUILLE = 0, 1, 2
 GRID_UNIFORM, GRID_TANH = 0, 1
 FP64, FP32_STORAGE, FP32_THEN_FP64 = 0, 1, 2
 CHI_SET, CHI_RET_FM = 0, 1
+XQ_HALF, XQ_FULL = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32_STORAGE, "fp32+fp64": FP32_THEN_FP64}
 SCHED_AUTO, SCHED_TILED, SCHED_RESIDENT = 0, 1, 2
 SCHEDULES = {"auto": SCHED_AUTO, "tiled": SCHED_TILED, "resident": SCHED_RESIDENT}
@@ -29,7 +30,8 @@ MOMENT_ROWS = ("n", "ux", "uy", "T", "qx", "qy", "Pxx", "Pxy")
 class CParams(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("flow", C.c_int32), ("nx", C.c_int32), ("grid", C.c_int32),
                 ("qx_half", C.c_int32), ("qy", C.c_int32), ("qz", C.c_int32), ("precision", C.c_int32),
-                ("j1_shear", C.c_int32), ("chi_model", C.c_int32), ("stretch", C.c_double), ("kn", C.c_double),
+                ("j1_shear", C.c_int32), ("chi_model", C.c_int32), ("x_quadrature", C.c_int32),
+                ("stretch", C.c_double), ("kn", C.c_double),
                 ("eta0", C.c_double), ("T_left", C.c_double), ("T_right", C.c_double), ("U_left", C.c_double),
                 ("U_right", C.c_double), ("accel_y", C.c_double), ("cfl", C.c_double), ("dt", C.c_double),
                 ("T_init", C.c_double)]
@@ -58,6 +60,7 @@ class Params:
     T_init: float = 0.0
     precision: str = "fp64"
     chi_model: str = "set"
+    x_quadrature: str = "half"      # "half" (Sec. III A 2) or "full" (order 2 qx_half, App. A)
 
     def to_c(self) -> CParams:
         p = CParams()
@@ -69,6 +72,7 @@ class Params:
         p.precision = PRECISIONS[self.precision]
         p.j1_shear = int(bool(self.j1_shear))
         p.chi_model = {"set": CHI_SET, "ret-fm": CHI_RET_FM}[self.chi_model]
+        p.x_quadrature = {"half": XQ_HALF, "full": XQ_FULL}[self.x_quadrature]
         p.stretch, p.kn, p.eta0 = float(self.stretch), float(self.kn), float(self.eta0)
         p.T_left, p.T_right, p.U_left, p.U_right = float(self.T_left), float(self.T_right), float(self.U_left), float(self.U_right)
         p.accel_y, p.cfl, p.dt, p.T_init = float(self.accel_y), float(self.cfl), float(self.dt), float(self.T_init)

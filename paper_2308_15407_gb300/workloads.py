@@ -67,14 +67,33 @@ def couette_family(count, seed, nx=200, qx_half=6, qy=6, qz=4, grid="tanh", prec
     return out
 
 
-def paper_geometry(R, eta0, qx_half=8, T_w=1.0, cells_per_sigma=100, precision="fp64"):
-    """The paper's own confinement (Sec. IV): a dense gas at rest between walls L = R sigma
-    apart whose molecule centres reach +-(L - sigma)/2, so the computational width is
-    D = (R - 1) sigma, i.e. sigma = D/(R - 1) in channel-width units; the Kn of Sec. II A,
-    referred to D, is 1/(6 sqrt(2) eta0 chi(eta0) (R - 1)), and Delta x = sigma/100.  The
-    Fischer-Methfessel contact value (Eq. chi_ret) gives the density layering next to the
-    walls.  1D reduced velocity set, walls at rest at temperature T_w."""
+def paper_geometry(R, eta0, qx_half=8, T_w=1.0, cells_per_sigma=100, precision="fp64", flow="rest", dT=0.0,
+                   U_w=0.0, a_y=0.0, qy=5, x_quadrature="half"):
+    """The paper's own confinement (Sec. IV): walls L = R sigma apart whose molecule centres
+    reach +-(L - sigma)/2, so the computational width is D = (R - 1) sigma, i.e.
+    sigma = D/(R - 1) in channel-width units; the Kn of Sec. II A, referred to D, is
+    1/(6 sqrt(2) eta0 chi(eta0) (R - 1)), and Delta x = sigma/cells_per_sigma (100 in the
+    paper).  The Fischer-Methfessel contact value (Eq. chi_ret) gives the density layering
+    next to the walls.
+
+    flow: "rest" (1D reduced, walls at T_w), "fourier" (1D reduced, walls at T_w -+ dT),
+    "couette" (2D reduced with qy, walls at -+U_w and T_w), "poiseuille" (2D reduced, walls at
+    rest, acceleration a_y).  The paper measures lengths in sigma (its L_c = R - 1) and speeds
+    in sqrt(k_B T_w/m); a_y is given in those units, v^2/sigma, and converted to the
+    channel-width units used here, a_y (R - 1).  x_quadrature: "half" (Sec. III A 2) or
+    "full" (order 2 qx_half, App. A)."""
     chi0 = (2.0 - eta0) / (2.0 * (1.0 - eta0) ** 3)
     kn = 1.0 / (6.0 * np.sqrt(2.0) * eta0 * chi0 * (R - 1.0))
-    return dict(nx=int(round(cells_per_sigma * (R - 1))), qx_half=qx_half, qy=0, qz=0, kn=float(kn), eta0=eta0,
-                T_left=T_w, T_right=T_w, chi_model="ret-fm", precision=precision, flow=0)
+    d = dict(nx=int(round(cells_per_sigma * (R - 1))), qx_half=qx_half, qy=0, qz=0, kn=float(kn), eta0=eta0,
+             T_left=T_w, T_right=T_w, chi_model="ret-fm", precision=precision, flow=0, x_quadrature=x_quadrature)
+    if flow == "rest":
+        return d
+    if flow == "fourier":
+        d.update(T_left=T_w - dT, T_right=T_w + dT)
+    elif flow == "couette":
+        d.update(qy=qy, U_left=-U_w, U_right=U_w, flow=1)
+    elif flow == "poiseuille":
+        d.update(qy=qy, accel_y=float(a_y * (R - 1.0)), flow=2)
+    else:
+        raise ValueError("flow must be rest, fourier, couette or poiseuille")
+    return d

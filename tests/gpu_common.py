@@ -19,7 +19,8 @@ def oracle_for(p):
     return ofd.Oracle(ofd.Params(nx=p.nx, qx_half=p.qx_half, qy=p.qy, qz=p.qz, kn=p.kn, eta0=p.eta0,
                                  T_left=p.T_left, T_right=p.T_right, U_left=p.U_left, U_right=p.U_right,
                                  accel_y=p.accel_y, grid=p.grid, stretch=p.stretch, cfl=p.cfl, dt=p.dt,
-                                 j1_shear=p.j1_shear, T_init=p.T_init, chi_model=p.chi_model))
+                                 j1_shear=p.j1_shear, T_init=p.T_init, chi_model=p.chi_model,
+                                 x_quadrature=p.x_quadrature))
 
 
 def compare(Mg, Mo, rel=1e-12, what=""):

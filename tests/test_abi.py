@@ -40,7 +40,7 @@ def test_abi_version_and_struct(F):
     lib = F.load()
     hdr = open(os.path.join(ROOT, "include", "fdlb.h")).read()
     assert lib.fdlb_abi_version() == int(re.search(r"#define FDLB_ABI_VERSION (\d+)", hdr).group(1))
-    assert ctypes.sizeof(F.CParams) == 4 * 10 + 8 * 11
+    assert ctypes.sizeof(F.CParams) == 4 * 11 + 4 + 8 * 11        # 11 int32, padding, 11 doubles
 
 
 def test_parameter_validation(F):
@@ -74,6 +74,22 @@ def test_chi_model_validation(F):
         F.workspace_bytes([F.Params(**{**base, "eta0": 0.0}, chi_model="ret-fm")])
 
 
+def test_x_quadrature_validation(F):
+    """The full-range x rule has order 2 qx_half <= 16; its tables hold 2 qx_half polynomials."""
+    base = dict(nx=64, qx_half=8, qy=4, qz=0, kn=0.1, eta0=0.1)
+    b_half = F.workspace_bytes([F.Params(**base)])
+    b_full = F.workspace_bytes([F.Params(**base, x_quadrature="full")])
+    assert b_full > b_half                      # w_k h_l(p_k) for l < 16 instead of l < 8
+    with pytest.raises(F.FdlbError):
+        F.workspace_bytes([F.Params(**{**base, "qx_half": 9}, x_quadrature="full")])
+    assert F.workspace_bytes([F.Params(**{**base, "qx_half": 9})]) > 0
+    lib = F.load()
+    c = F.Params(**base).to_c()
+    c.x_quadrature = 2
+    assert lib.fdlb_workspace_bytes((F.CParams * 1)(c), 1) == 0
+    assert b"x_quadrature" in lib.fdlb_last_error(None)
+
+
 def test_two_phase_precision_workspace(F):
     """FP32-then-FP64 instances hold f at its FP64 size; unknown precisions are rejected."""
     base = dict(nx=64, qx_half=4, qy=4, qz=4, kn=0.1, eta0=0.1)
@@ -100,7 +116,7 @@ def test_library_half_range_rule_matches_oracle(F, Q):
     np.testing.assert_allclose(w, r.weights, rtol=5e-14, atol=1e-17)
 
 
-@pytest.mark.parametrize("Q", [2, 3, 4, 6, 8])
+@pytest.mark.parametrize("Q", [2, 3, 4, 6, 8, 10, 12, 16])
 def test_library_full_range_rule_matches_oracle(F, Q):
     x, w = F.quadrature("full", Q)
     r = qd.full_range_rule(Q)

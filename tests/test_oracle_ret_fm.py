@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from oracle import fdlb as ofd
 
@@ -99,3 +100,24 @@ def test_paper_geometry_parameters():
         assert abs((1.0 / d["nx"]) / sigma - 0.01) < 1e-12
         kn_L = d["kn"] * (R - 1) / R
         assert abs(kn_L - ofd.knudsen(eta0, R)) < 1e-15
+
+
+def test_paper_geometry_flows():
+    """The paper's flows in its geometry: walls at T0 -+ dT (Fourier), -+U_0 (Couette), the
+    acceleration given in v^2/sigma converted to channel-width units (Poiseuille); every set
+    is accepted by the oracle and keeps Delta x = sigma/cells_per_sigma."""
+    from paper_2308_15407_gb300 import workloads
+    R, eta0 = 10, 0.01
+    f = workloads.paper_geometry(R, eta0, flow="fourier", dT=0.5, cells_per_sigma=10)
+    assert (f["T_left"], f["T_right"], f["qy"]) == (0.5, 1.5, 0)
+    c = workloads.paper_geometry(R, eta0, flow="couette", U_w=1.0, cells_per_sigma=10, x_quadrature="full")
+    assert (c["U_left"], c["U_right"], c["qy"], c["x_quadrature"]) == (-1.0, 1.0, 5, "full")
+    p = workloads.paper_geometry(R, eta0, flow="poiseuille", a_y=0.001, cells_per_sigma=10)
+    sigma = ofd.sphere_diameter(eta0, p["kn"])
+    assert abs(p["accel_y"] - 0.001 / sigma) < 1e-15                  # a [v^2/sigma] = a/sigma [v^2/D]
+    for d in (f, c, p):
+        assert d["nx"] == 90
+        keys = {k: v for k, v in d.items() if k not in ("precision",)}
+        ofd.Oracle(ofd.Params(**{**keys, "chi_model": "ret-fm"}))
+    with pytest.raises(ValueError):
+        workloads.paper_geometry(R, eta0, flow="shear")
