@@ -1,0 +1,48 @@
+"""The comparison of App. A in the paper's geometry (R = 10, eta0 = 0.01; Fourier dT = 0.5,
+Couette U_w = 1, Poiseuille a_y = 0.001 in v^2/sigma), with Delta x = sigma/20: steady states
+to residual 1e-10 in FP64 for half-range orders 4, 8, 16 per side and full-range orders 8, 12,
+16.  eps = max |M - M_ref| / (max M_ref - min M_ref) (the error measure of Sec. IV) against
+half-range order 16 (32 x-velocities), M = T (Fourier) or u_y.  With as many velocities, the
+full-range rule misses the wall discontinuity: its error is several times the half-range one,
+and it falls only slowly with the order."""
+import numpy as np
+import pytest
+
+from gpu_common import lib
+
+pytestmark = pytest.mark.gpu
+
+FLOWS = [("fourier", dict(dT=0.5), "T"), ("couette", dict(U_w=1.0), "uy"), ("poiseuille", dict(a_y=0.001), "uy")]
+CFGS = [("half", 16), ("half", 4), ("half", 8), ("full", 4), ("full", 6), ("full", 8)]
+
+
+def test_full_range_needs_more_velocities_than_half_range():
+    F = lib()
+    from paper_2308_15407_gb300 import workloads as W
+    dicts = [W.paper_geometry(10, 0.01, qx_half=q, cells_per_sigma=20, flow=fl, x_quadrature=xq, **kw)
+             for fl, kw, _ in FLOWS for xq, q in CFGS]
+    s = F.Solver([F.Params(**d) for d in dicts])
+    for _ in range(60):
+        s.step(2000, 1e-10)
+        if np.all(s.status()[1] != F.ACTIVE):
+            break
+    _, st, _ = s.status()
+    assert np.all(st == F.CONVERGED), st
+    for fi, (fl, _, key) in enumerate(FLOWS):
+        base = fi * len(CFGS)
+        ref = s.moments(base)[key]
+        span = ref.max() - ref.min()
+        eps = {c: np.max(np.abs(s.moments(base + j)[key] - ref)) / span for j, c in enumerate(CFGS) if j}
+        # equal numbers of x-velocities (8 and 16): half-range is the more accurate (measured:
+        # factors 2.2-7 at 8 velocities, 7-15 at 16)
+        assert eps[("half", 4)] < 0.6 * eps[("full", 4)], (fl, eps)
+        assert eps[("half", 8)] < 0.3 * eps[("full", 8)], (fl, eps)
+        # the half-range error falls by a factor > 3 from 8 to 16 velocities (measured 4-5.7)
+        assert eps[("half", 8)] < eps[("half", 4)] / 3, (fl, eps)
+        if fl != "couette":
+            # full range converges toward the half-range reference, slowly (factor < 3 over 8 -> 16)
+            assert eps[("full", 8)] < eps[("full", 6)] < eps[("full", 4)], (fl, eps)
+            assert eps[("full", 8)] > eps[("full", 4)] / 3, (fl, eps)
+    # Poiseuille mass flow rate: full range underestimates it, by less as the order grows
+    mfr = [float(np.mean(s.moments(2 * len(CFGS) + j)["n"] * s.moments(2 * len(CFGS) + j)["uy"])) for j in (0, 3, 4, 5)]
+    assert mfr[1] < mfr[2] < mfr[3] < mfr[0]
