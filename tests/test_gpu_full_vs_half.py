@@ -34,7 +34,7 @@ def test_full_range_needs_more_velocities_than_half_range():
         span = ref.max() - ref.min()
         eps = {c: np.max(np.abs(s.moments(base + j)[key] - ref)) / span for j, c in enumerate(CFGS) if j}
         # equal numbers of x-velocities (8 and 16): half-range is the more accurate (measured:
-        # factors 2.2-7 at 8 velocities, 7-15 at 16)
+        # factors 2.2-7.3 at 8 velocities, 6.8-15 at 16)
         assert eps[("half", 4)] < 0.6 * eps[("full", 4)], (fl, eps)
         assert eps[("half", 8)] < 0.3 * eps[("full", 8)], (fl, eps)
         # the half-range error falls by a factor > 3 from 8 to 16 velocities (measured 4-5.7)
