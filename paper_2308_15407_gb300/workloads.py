@@ -1,7 +1,8 @@
 """Seeded synthetic workloads (parameter sets only; no arithmetic of the method).
 
 Used by the tests and the benchmark to build identical inputs for the CUDA path and for the
-oracle.  Each function returns a list of plain dicts with the keys of ``fdlb.Params``.
+oracle.  Each function returns a list of plain dicts with the keys of ``fdlb.Params``
+(``knudsen_sweep`` also returns the confinement ratio and Knudsen number of each).
 """
 import numpy as np
 
@@ -97,3 +98,44 @@ def paper_geometry(R, eta0, qx_half=8, T_w=1.0, cells_per_sigma=100, precision="
     else:
         raise ValueError("flow must be rest, fourier, couette or poiseuille")
     return d
+
+
+def eta_for_knudsen(kn_L, R, eta_hi=0.49):
+    """eta0 with 1/(6 sqrt(2) eta0 chi(eta0) R) = kn_L (the Kn of Sec. II A referred to
+    L = R sigma), by bisection on the increasing eta0 chi(eta0); None when kn_L needs
+    eta0 >= eta_hi."""
+    target = 1.0 / (6.0 * np.sqrt(2.0) * kn_L * R)
+    g = lambda e: e * (2.0 - e) / (2.0 * (1.0 - e) ** 3)
+    if g(eta_hi) < target:
+        return None
+    lo, hi = 0.0, eta_hi
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if g(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def knudsen_sweep(R_values=(2, 5, 10, 20), points=8, kn_max=1.0, eta_max=0.2, a_y=0.001, qx_half=8, qy=4,
+                  cells_per_sigma=20, min_cells=60, precision="fp32"):
+    """Poiseuille mass-flow sweep of Sec. IV (mass flow rate against Kn for several R) in the
+    paper's geometry: for each R, `points` Knudsen numbers (referred to L = R sigma) spaced
+    logarithmically from the smallest one reachable with eta0 <= eta_max (higher densities
+    are linearly unstable with these velocity sets) to kn_max; eta0 from eta_for_knudsen;
+    acceleration a_y in v^2/sigma; Delta x = sigma/cells_per_sigma, at least min_cells cells.
+    Returns (dicts, tags) with tags[i] = (R, Kn_L, eta0)."""
+    dicts, tags = [], []
+    for R in R_values:
+        g_max = eta_max * (2.0 - eta_max) / (2.0 * (1.0 - eta_max) ** 3)
+        kn_min = 1.0 / (6.0 * np.sqrt(2.0) * g_max * R)
+        for kn in np.geomspace(kn_min * 1.0001, kn_max, points):
+            eta0 = eta_for_knudsen(float(kn), R)
+            cps = max(cells_per_sigma, int(np.ceil(min_cells / (R - 1.0))))
+            d = paper_geometry(R, eta0, qx_half=qx_half, cells_per_sigma=cps, precision=precision,
+                               flow="poiseuille", a_y=a_y, qy=qy)
+            dicts.append(d)
+            tags.append((R, float(kn), float(eta0)))
+    return dicts, tags
+

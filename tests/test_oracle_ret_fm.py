@@ -121,3 +121,21 @@ def test_paper_geometry_flows():
         ofd.Oracle(ofd.Params(**{**keys, "chi_model": "ret-fm"}))
     with pytest.raises(ValueError):
         workloads.paper_geometry(R, eta0, flow="shear")
+
+
+def test_knudsen_sweep_parameters():
+    """The mass-flow sweep's instances: Kn referred to L = R sigma is the closed form of Sec. II A
+    at the chosen eta0 (within the stable eta0 <= 0.2), spaced from the smallest reachable Kn to
+    1 for each R, in the paper's geometry with the acceleration converted from v^2/sigma."""
+    from paper_2308_15407_gb300 import workloads
+    dicts, tags = workloads.knudsen_sweep(R_values=(2, 10), points=5)
+    assert len(dicts) == 10
+    for d, (R, kn, eta0) in zip(dicts, tags):
+        assert 0 < eta0 <= 0.2 + 1e-12 and d["eta0"] == eta0
+        assert abs(ofd.knudsen(eta0, R) / kn - 1) < 1e-10
+        assert abs(d["kn"] * (R - 1) / R / kn - 1) < 1e-10
+        assert d["nx"] >= 60 and d["flow"] == 2 and d["chi_model"] == "ret-fm"
+        assert abs(d["accel_y"] - 0.001 * (R - 1)) < 1e-15
+    kns = [t[1] for t in tags[:5]]
+    assert abs(kns[-1] - 1.0) < 1e-12 and all(a < b for a, b in zip(kns, kns[1:]))
+    assert workloads.eta_for_knudsen(1e-4, 2) is None
