@@ -4,7 +4,8 @@
 //   k_nodal    per node: chi (Eq. chi), Pr (Eq. prandtl), tau (Eqs. viscosity, tau),
 //              6th-order gradients (Sec. III B 3), the 13 monomial coefficients of
 //              f^S + tau J1 (Sec. II A, Eq. j1) and their projections onto the
-//              half-range (Sec. III A 2) and full-range (App. A) velocity sets;
+//              half-range (Sec. III A 2) and full-range (App. A) velocity sets (on x
+//              either rule);
 //              per instance: the wall densities n_w (Sec. III B);
 //   k_update   per (velocity, node): WENO-5 fluxes (Sec. III B 2) with the
 //              diffuse-reflection closure, the p_y-derivative force (App. A,
