@@ -100,3 +100,46 @@ def test_free_molecular_couette():
     pex = -math.sqrt(1 / (2 * math.pi)) * (UR - UL)
     assert np.abs(M["Pxy"] / pex - 1).max() < 1e-10
     np.testing.assert_allclose(M["uy"], 0.5 * (UL + UR), atol=1e-10)
+
+
+@pytest.mark.parametrize("shear", [False, True])
+def test_small_kn_couette_shear_stress(shear):
+    """Chapman-Enskog limit (Kn = 0.01): from the local equilibrium of a linear u_y profile,
+    after ~18 relaxation times the bulk kinetic shear stress is -tau n T d_x u_y with
+    tau n T = mu of Eq. (viscosity); with the shear term of Eq. (j1) the J1 part adds
+    (2/5) b rho chi of it.  The bar (1e-4) leaves room for the O(Kn^2) and the residue of the
+    start-up transient."""
+    kn, eta0 = 0.01, 0.1
+    # n = 1.2 and T = 1.3 so that a wrong n or T in tau = mu/(n T) would show
+    o = ofd.Oracle(ofd.Params(nx=40, qx_half=4, qy=4, qz=0, kn=kn, eta0=eta0, U_left=-0.1, U_right=0.1,
+                              T_left=1.3, T_right=1.3, flow=ofd.COUETTE, j1_shear=shear))
+    o.set_profiles(np.full(40, 1.2), 0.2 * o.x, np.full(40, 1.3))
+    o.step(60)
+    M = o.moments()
+    i = np.arange(17, 23)
+    dudx = (M["uy"][i + 1] - M["uy"][i - 1]) / (o.x[i + 1] - o.x[i - 1])
+    n, T = M["n"][i], M["T"][i]
+    eta = eta0 * n
+    chi = (2 - eta) / (2 * (1 - eta) ** 3)
+    chi0 = (2 - eta0) / (2 * (1 - eta0) ** 3)
+    brho = 4 * eta
+    mu = 5 / 16 * math.sqrt(2 * math.pi) * chi0 * kn * np.sqrt(T) * (
+        1 / chi + 0.8 * brho + 4 / 25 * (1 + 12 / math.pi) * brho ** 2 * chi)
+    expect = mu * (1 + 0.4 * brho * chi if shear else 1.0)
+    assert np.max(np.abs(-M["Pxy"][i] / dudx / expect - 1)) < 1e-4
+
+
+def test_dense_terms_vanish_continuously():
+    """eta0 -> 0: the Couette profiles at eta0 = 1e-6 and 2e-6 differ from the dilute ones by
+    amounts proportional to eta0 (no term survives at eta0 = 0 with an O(1) jump)."""
+    kw = dict(nx=24, qx_half=4, qy=4, qz=0, kn=0.1, U_left=-0.3, U_right=0.3, grid="tanh", j1_shear=True)
+    M = []
+    for eta0 in (0.0, 1e-6, 2e-6):
+        o = ofd.Oracle(ofd.Params(eta0=eta0, **kw))
+        o.step(80)
+        M.append(o.moments())
+    for k in ("n", "uy", "T", "Pxy"):
+        d1, d2 = M[1][k] - M[0][k], M[2][k] - M[0][k]
+        scale = np.max(np.abs(d2))
+        assert scale > 1e-9, k                      # the dense terms do act
+        assert np.max(np.abs(d2 - 2 * d1)) < 1e-4 * scale, k
