@@ -222,6 +222,20 @@ def solve(s, F, nx, warm=None):
             raise
 
 
+def combine_ranks(dist, ms, updates, solved, device):
+    """Whole-job totals of the timed region: the slowest rank's milliseconds (MAX over ranks)
+    and the node-velocity updates and converged instances of all ranks (SUM); every rank
+    receives them.  dist is None for a single process."""
+    import torch
+    if dist is None:
+        return float(ms), float(updates), float(solved)
+    tm = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    tu = torch.tensor([float(updates), float(solved)], dtype=torch.float64, device=device)
+    dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+    return float(tm.item()), float(tu[0].item()), float(tu[1].item())
+
+
 def run_fdlb(args):
     import numpy as np
     import torch
@@ -293,15 +307,7 @@ def run_fdlb(args):
         barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     sched = "%s (cluster of %d CTAs available)" % s.schedule()
-    t = torch.tensor([ms, updates, float(solved)], dtype=torch.float64, device=f"cuda:{local}")
-    if dist is not None:
-        tm = t[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        tu = t[1:].clone()
-        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
-        ms_max, updates_all, solved_all = float(tm.item()), float(tu[0].item()), float(tu[1].item())
-    else:
-        ms_max, updates_all, solved_all = ms, updates, float(solved)
+    ms_max, updates_all, solved_all = combine_ranks(dist, ms, updates, solved, f"cuda:{local}")
     value = updates_all / (ms_max * 1e-3)
     solves_per_s = solved_all / (ms_max * 1e-3)
     _, status, _ = s.status()
