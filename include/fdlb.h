@@ -187,6 +187,13 @@ int fdlb_moments(fdlb_ctx* ctx, int32_t inst, double* host_out);
 /* Per-instance last residual, status and step count (synchronises).  Any pointer may be NULL. */
 int fdlb_status(fdlb_ctx* ctx, double* residual, int32_t* status, int64_t* steps);
 
+/* Per-instance residual of the last step (synchronises): host_out[count] receives the
+ * residual that fdlb_status reports, the largest of the step's changes of n and T (relative)
+ * and of u_x and u_y, each in the cell-width-weighted L2 norm over the channel (the
+ * steady-state measure; the paper gives none).  Errors: FDLB_EINVAL (null ctx or host_out),
+ * FDLB_ECUDA. */
+int fdlb_residual(fdlb_ctx* ctx, double* host_out);
+
 /* Reset instance `inst` to the projected local equilibrium with the given profiles
  * (u_x = 0; host arrays of nx values; n > 0, T > 0) and mark it ACTIVE with 0 steps
  * (an FDLB_FP32_THEN_FP64 instance restarts in its FP32 phase). */

@@ -1012,6 +1012,12 @@ extern "C" int fdlb_status(fdlb_ctx* c, double* residual, int32_t* status, int64
     return rc;
 }
 
+extern "C" int fdlb_residual(fdlb_ctx* c, double* host_out) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_residual: null context");
+    if (!host_out) return fail(c, FDLB_EINVAL, "fdlb_residual: null output");
+    return fdlb_status(c, host_out, nullptr, nullptr);
+}
+
 extern "C" int fdlb_run(fdlb_ctx* c, double tol, int64_t max_steps, int64_t check_every, double timeout_s) {
     if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_run: null context");
     if (!(tol > 0) || max_steps < 0 || check_every < 1 || !(timeout_s > 0)) return fail(c, FDLB_EINVAL, "fdlb_run: bad arguments");

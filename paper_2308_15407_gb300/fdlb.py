@@ -103,6 +103,7 @@ def load() -> C.CDLL:
         "fdlb_run": (C.c_int, [vp, C.c_double, C.c_int64, C.c_int64, C.c_double]),
         "fdlb_moments": (C.c_int, [vp, C.c_int32, dp]),
         "fdlb_status": (C.c_int, [vp, dp, ip, lp]),
+        "fdlb_residual": (C.c_int, [vp, dp]),
         "fdlb_precision": (C.c_int, [vp, ip, lp]),
         "fdlb_set_schedule": (C.c_int, [vp, C.c_int32]),
         "fdlb_get_schedule": (C.c_int, [vp, ip, ip]),
@@ -244,6 +245,12 @@ class Solver:
         self._check(self.lib.fdlb_status(self.ctx, _dptr(r), s.ctypes.data_as(C.POINTER(C.c_int32)),
                                          st.ctypes.data_as(C.POINTER(C.c_int64))))
         return r, s, st
+
+    def residual(self) -> np.ndarray:
+        """Per-instance residual of the last step (the first array of ``status``)."""
+        r = np.zeros(self.count)
+        self._check(self.lib.fdlb_residual(self.ctx, _dptr(r)))
+        return r
 
     def set_schedule(self, schedule: str):
         """'auto' (time both on the first long step call), 'tiled' or 'resident'."""

@@ -74,6 +74,16 @@ def test_chi_model_validation(F):
         F.workspace_bytes([F.Params(**{**base, "eta0": 0.0}, chi_model="ret-fm")])
 
 
+def test_null_context_calls_fail_cleanly(F):
+    """Calls on a null context return FDLB_EINVAL without touching a device."""
+    lib = F.load()
+    out = np.zeros(4)
+    assert lib.fdlb_residual(None, F._dptr(out)) == F.FDLB_EINVAL
+    assert b"fdlb_residual" in lib.fdlb_last_error(None)
+    assert lib.fdlb_status(None, F._dptr(out), None, None) == F.FDLB_EINVAL
+    assert lib.fdlb_step(None, 1, 0.0) == F.FDLB_EINVAL
+
+
 def test_x_quadrature_validation(F):
     """The full-range x rule has order 2 qx_half <= 16; its tables hold 2 qx_half polynomials."""
     base = dict(nx=64, qx_half=8, qy=4, qz=0, kn=0.1, eta0=0.1)

@@ -40,6 +40,7 @@ def test_first_step_residual_every_instance():
     s = F.Solver([F.Params(**d) for d in HETERO])
     s.step(1)
     r, st, ns = s.status()
+    assert np.array_equal(s.residual(), r)
     for i, d in enumerate(HETERO):
         o = oracle_for(F.Params(**d))
         o.step(1)
