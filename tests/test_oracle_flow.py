@@ -143,3 +143,27 @@ def test_dense_terms_vanish_continuously():
         scale = np.max(np.abs(d2))
         assert scale > 1e-9, k                      # the dense terms do act
         assert np.max(np.abs(d2 - 2 * d1)) < 1e-4 * scale, k
+
+
+def test_small_kn_fourier_law():
+    """Dilute steady Fourier flow at Kn = 0.02: with mu = mu0 sqrt(T) and Pr = 2/3 the
+    conductivity is (15/4) mu, so q_x = -(5/2) mu0 d(T^(3/2))/dx is uniform and T^(3/2) is
+    linear in the bulk (T itself is visibly curved); checked to O(Kn^2) outside the Knudsen
+    layers."""
+    kn, dT = 0.02, 0.05
+    o = ofd.Oracle(ofd.Params(nx=24, qx_half=4, qy=0, qz=0, kn=kn, eta0=0.0, T_left=1 - dT, T_right=1 + dT))
+    o.run_to_residual(1e-9, 40000, check_every=200)
+    assert o.last_residual < 1e-9
+    M = o.moments()
+    bulk = np.abs(o.x) < 0.3
+    A = np.vstack([o.x[bulk], np.ones(bulk.sum())]).T
+
+    def fit(y):
+        c, *_ = np.linalg.lstsq(A, y[bulk], rcond=None)
+        return c, np.max(np.abs(y[bulk] - A @ c)) / np.ptp(y[bulk])
+
+    c15, dev15 = fit(M["T"] ** 1.5)
+    _, dev1 = fit(M["T"])
+    assert dev15 < 2e-4 and dev1 > 1e-3
+    mu0_1 = 5 / 16 * math.sqrt(2 * math.pi) * kn
+    np.testing.assert_allclose(M["qx"][bulk], -2.5 * mu0_1 * c15[0], rtol=3e-4)
