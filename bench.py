@@ -438,6 +438,20 @@ def run_fdlb(args):
         plain = {"solves_per_s": 1.0 / sec, "steps": n64, "seconds": sec,
                  "node_vel_updates_per_s": n64 * s64.nx[0] * s64.nvel[0] / sec,
                  "instance": "eta0=0.1, Kn=0.5, FP64 storage, alone in its context"}
+        # profile error of the FP32 form: the same instance in the batched FP32-storage cold
+        # solve above against this FP64 solve, both stopped at residual TOL
+        try:
+            i32 = [i for i, p in enumerate(params) if p.eta0 == 0.1 and p.kn == 0.5][0]
+            M32, M64 = s.moments(i32), s64.moments(0)
+            plain["fp32_vs_fp64_profiles"] = {
+                "what": "batched FP32 storage vs plain FP64, same instance, both at residual %g" % TOL,
+                "n_rel": float(np.max(np.abs(M32["n"] - M64["n"]) / M64["n"])),
+                "T_rel": float(np.max(np.abs(M32["T"] - M64["T"]) / M64["T"])),
+                "uy_abs": float(np.max(np.abs(M32["uy"] - M64["uy"]))),
+                "Pxy_rel": float(np.max(np.abs(M32["Pxy"] - M64["Pxy"])) / np.max(np.abs(M64["Pxy"]))),
+                "steps_fp32_fp64": [int(done_c[i32]), n64]}
+        except Exception as e:                       # reporting only: never fail the bench line
+            plain["fp32_vs_fp64_profiles"] = {"error": str(e)[:200]}
         s64.close()
 
     # ---- CPU baseline (rank 0, N = 1 only)
