@@ -197,6 +197,10 @@ class Solver:
         base = self.ws.data_ptr()
         ptr = (base + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if self.stream != torch.cuda.current_stream(self.device):
+            # the library's work runs on self.stream: keep the caching allocator from reusing
+            # the workspace before that work has finished
+            self.ws.record_stream(self.stream)
         self.ctx = C.c_void_p()
         rc = self.lib.fdlb_create(C.byref(self.ctx), arr, self.count, C.c_void_p(ptr), nbytes,
                                   C.c_void_p(self.stream.cuda_stream))
