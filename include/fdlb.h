@@ -27,7 +27,8 @@
  *    asynchronous; every call that returns host data synchronises that stream.
  *  - Layout of f in the workspace: per instance, f[kappa][node] (node index
  *    contiguous, row stride rounded up to 32), kappa = kx * T_c + t with
- *    kx = 0..Q-1 for +p_k and Q..2Q-1 for -p_k (half-range nodes, Eq. hh_pk),
+ *    kx = 0..Q-1 for +p_k and Q..2Q-1 for -p_k (half-range nodes, Eq. hh_pk, or the
+ *    positive nodes of the full-range rule of order 2Q with FDLB_XQ_FULL),
  *    t the transverse index: t = ky*Q_z + kz (unreduced), t = 2 ky + slot
  *    (2D reduced, slot 0 = phi, 1 = theta), t = slot (1D reduced).
  */
@@ -220,9 +221,10 @@ int fdlb_set_state(fdlb_ctx* ctx, int32_t inst, const void* host, size_t bytes);
  *             with large batches.
  *   RESIDENT: one thread-block cluster per instance (up to 16 CTAs) runs whole steps in one
  *             launch, the phases separated by cluster barriers; instances advance
- *             independently and a converged instance's cluster exits.  Suits small batches
- *             and long solves, where the tiled schedule is bound by launch gaps and by the
- *             latency of each phase.
+ *             independently and a converged instance's cluster exits.  It has no launches
+ *             inside a step; on the GB300 the tiled schedule still measured faster on every
+ *             workload tried (one instance: 113 against 244 us per RK3 step), because it
+ *             spreads an instance's latency-bound items over more SMs than a cluster has.
  *   AUTO:     (default) the first fdlb_step call with at least FDLB_AUTOTUNE_STEPS steps
  *             times both (its own steps, half each) and keeps the faster; shorter calls use
  *             TILED until then.
