@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define FDLB_ABI_VERSION 5
+#define FDLB_ABI_VERSION 6
 
 /* Return codes. */
 #define FDLB_OK            0
@@ -166,6 +166,15 @@ void fdlb_destroy(fdlb_ctx* ctx);
 /* Number of instances, nodes of instance i, velocities of instance i. */
 int fdlb_info(const fdlb_ctx* ctx, int32_t inst, int32_t* nx, int32_t* nvel, double* dt);
 
+/* How the tiled schedule splits instance `inst` (Sec. III B's per-node / per-velocity
+ * structure; the split is a property of the batch, not of the method): *chunk = velocities
+ * per update block, *chunks_per_tile = update blocks per 32-node tile (> 1: the blocks'
+ * partial moment sums are added in chunk order by the last block of the tile), *tiles =
+ * 32-node tiles.  The chunk is 16 velocities for batches of fewer than 38 tiles, 32 up to
+ * 1215 tiles, and the whole velocity set (at most 256 per block) from 1216 tiles on.  Any
+ * output pointer may be NULL.  Errors: FDLB_EINVAL (null context, instance out of range). */
+int fdlb_layout(const fdlb_ctx* ctx, int32_t inst, int32_t* chunk, int32_t* chunks_per_tile, int32_t* tiles);
+
 /* Advance every ACTIVE instance by nsteps RK3 steps (asynchronous).  Each step computes the
  * per-step residual of every instance (change of n, T, u_x, u_y in the cell-width-weighted
  * L2 norm; relative for n and T) and marks non-finite or unphysical instances FAILED.
@@ -252,8 +261,11 @@ int fdlb_get_schedule(const fdlb_ctx* ctx, int32_t* schedule, int32_t* cluster_c
 int fdlb_profile(fdlb_ctx* ctx, int32_t on);
 int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 
-/* Largest scratch fdlb_step_noalloc can use (8 MiB): enough for one instance of e.g.
- * nx = 400 with 16 x 6 x 6 velocities in FP64. */
+/* Largest scratch fdlb_step_noalloc can use (8 MiB = 8,388,608 B): enough for one instance
+ * of nx = 400 with 16 x-velocities (qx_half = 8) x 6 x 6 in FP64 (8,218,624 B, the
+ * Poiseuille set-up of Sec. IV), or the 200-node Couette instance with 12 x 6 x 4 velocities
+ * (1.7 MB in FP32 storage).  fdlb_workspace_bytes(params, 1) is the amount an instance needs;
+ * nx = 400 with qx_half = 16 x 6 x 6 (15.9 MB in FP64) is rejected. */
 #define FDLB_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 
 /* Stepping without any device allocation, for callers that cannot call cudaMalloc (or any
@@ -265,14 +277,17 @@ int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* la
  * Advances ONE instance (params) by nsteps RK3 steps in place: dev_f (f_bytes bytes of
  * device memory) holds its f in the layout described at the top of this file, i.e.
  * K * ceil(nx/32)*32 values of double (FDLB_FP64) or float (FDLB_FP32_STORAGE) with
- * K = 2 qx_half * T_c (FDLB_FP32_THEN_FP64 is rejected with FDLB_EINVAL).  If dev_moments is not NULL it receives the 8 x nx moment rows of
- * the result (as fdlb_moments, device memory).  All scratch lives in one static device
- * array of FDLB_NOALLOC_SCRATCH_BYTES that every device loading the library holds until the
- * process exits; instances that need more are rejected with FDLB_ENOMEM.  The array is
- * shared by every call and keeps the last call's contents (each call rebuilds what it
- * reads), so calls that overlap on the GPU race: serialise them.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Synchronises `stream`.
+ * K = 2 qx_half * T_c (FDLB_FP32_THEN_FP64 is rejected with FDLB_EINVAL).  If dev_moments
+ * is not NULL it receives the 8 x nx moment rows of the result (as fdlb_moments, device
+ * memory, 8 nx doubles).  All scratch lives in one static device array of
+ * FDLB_NOALLOC_SCRATCH_BYTES that every device loading the library holds until the process
+ * exits; instances that need more are rejected with FDLB_ENOMEM.  The array is shared by
+ * every call and keeps the last call's contents (each call rebuilds what it reads), so calls
+ * that overlap on the GPU race: serialise them.  Each call launches its kernels one by one
+ * (it builds no CUDA graph), uploads its tables from the host and synchronises `stream`
+ * twice, so it must never be called while its stream, or the process, is being captured into
+ * a CUDA graph.  The first call on a device also looks up the array's device address
+ * (cudaGetSymbolAddress).
  * Errors: FDLB_EINVAL (bad params or f_bytes), FDLB_ENOMEM, FDLB_ECUDA. */
 int fdlb_step_noalloc(const fdlb_params* params, void* dev_f, size_t f_bytes, int64_t nsteps,
                       double* dev_moments, void* stream);

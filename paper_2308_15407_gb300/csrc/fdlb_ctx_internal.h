@@ -10,5 +10,6 @@ int ctx_f_buffer(fdlb_ctx* c, int inst, void** f, size_t* bytes);            // 
 int ctx_reanchor(fdlb_ctx* c, int inst);                                      // moments of F, residual anchor, ACTIVE
 int ctx_moment_rows(fdlb_ctx* c, int inst, const double** rows, int* ld, int* nx);
 cudaStream_t ctx_stream(fdlb_ctx* c);
+void ctx_direct_launches(fdlb_ctx* c);                                        // never capture or instantiate a graph
 void set_global_error(const std::string& msg);
 }  // namespace fdlb

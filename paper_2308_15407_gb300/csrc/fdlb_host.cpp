@@ -835,6 +835,16 @@ extern "C" int fdlb_info(const fdlb_ctx* ctx, int32_t inst, int32_t* nx, int32_t
     return FDLB_OK;
 }
 
+extern "C" int fdlb_layout(const fdlb_ctx* ctx, int32_t inst, int32_t* chunk, int32_t* chunks_per_tile, int32_t* tiles) {
+    if (!ctx) return fail(nullptr, FDLB_EINVAL, "fdlb_layout: null context");
+    if (inst < 0 || inst >= ctx->count) return fail(const_cast<fdlb_ctx*>(ctx), FDLB_EINVAL, "fdlb_layout: instance out of range");
+    const Inst& I = ctx->inst[inst];
+    if (chunk) *chunk = I.ukc;
+    if (chunks_per_tile) *chunks_per_tile = I.mgroups;
+    if (tiles) *tiles = (I.N + TILE - 1) / TILE;
+    return FDLB_OK;
+}
+
 static const int GRAPH_STEPS = 16;
 static const int RESIDENT_CHUNK = 256;     // steps per resident launch
 
@@ -1250,6 +1260,10 @@ int ctx_moment_rows(fdlb_ctx* c, int inst, const double** rows, int* ld, int* nx
 }
 
 cudaStream_t ctx_stream(fdlb_ctx* c) { return c->stream; }
+
+// fdlb_step then launches every step's kernels directly: no stream capture, no graph
+// instantiation (which may allocate inside the driver).
+void ctx_direct_launches(fdlb_ctx* c) { c->graph_failed = true; }
 
 void set_global_error(const std::string& msg) { g_err = msg; }
 

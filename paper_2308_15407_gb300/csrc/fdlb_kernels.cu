@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <mutex>
+
 namespace fdlb {
 
 __constant__ double c_inv[13] = {0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12};
@@ -1534,8 +1536,18 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
         for (int a = 0; a < 4; ++a) tgt += stab[(a * 2 * Q + kx) * TILE + lane] * stab[(8 * Q + a * Tc + t) * TILE + lane];
         const C fi = v[3];
         L += (tgt - fi) * invtau;
-        C out = cb * (fi + dt * L);
-        if (stage != 1) out += ca * Fk;
+        C out;
+        if constexpr (sizeof(C) == 4) {
+            // FP32: the same combination written as an increment of F, F + cb ((f - F) + dt L)
+            // (stage 1: f + dt L).  In the printed form ca F + cb (f + dt L) the rounded
+            // weights (float) 1/3 + (float) 2/3 = 1 + 3e-8 scale a steady f up by half an ulp
+            // every step, a mass drift of ~1e-3 over a solve; the increment form has no such
+            // bias and leaves f unchanged where the update vanishes.
+            out = stage == 1 ? fi + dt * L : Fk + cb * ((fi - Fk) + dt * L);
+        } else {
+            out = cb * (fi + dt * L);
+            if (stage != 1) out += ca * Fk;
+        }
         dst[(size_t)k * ld + i] = (S)out;
         fo[(k - k0) * TILE + lane] = (S)out;
     }
@@ -1656,6 +1668,33 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(Inst* insts, const 
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
+// Kernel attributes (dynamic shared memory above 48 KB, non-portable cluster sizes) and the
+// __constant__ tables are per device: each device keeps its own record of what was set, and
+// a mutex serialises the updates.  Attributes only ever grow, so contexts created earlier on
+// a device keep launching.
+namespace {
+constexpr int kMaxDevices = 64;
+struct DevAttr {
+    bool consts = false;
+    int nodal = 0;
+    size_t mom64 = 0, mom32 = 0, upd64 = 0, upd32 = 0;
+    size_t res[2] = {0, 0};
+    bool nonport[2] = {false, false};
+};
+std::mutex g_attr_mu;
+DevAttr g_attr[kMaxDevices];
+
+// Record of the current device (the caller holds g_attr_mu).
+cudaError_t dev_attr(DevAttr** out) {
+    int d = -1;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= kMaxDevices) return cudaErrorInvalidDevice;
+    *out = &g_attr[d];
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_setup(const Inst* d_inst, int count, cudaStream_t s) {
     k_setup<<<count, 128, 0, s>>>(const_cast<Inst*>(d_inst));
     k_profiles<double><<<count, 128, 0, s>>>(const_cast<Inst*>(d_inst), -1);
@@ -1677,18 +1716,21 @@ size_t update_smem_bytes(int ntab, int ukc, size_t c, size_t s) { return upd_sme
 
 cudaError_t launch_moments(const Inst* d_inst, const Work* d_upd, int n_upd, int buf, int ukc_max, bool f64, bool f32,
                            cudaStream_t s) {
-    static size_t done64 = 0, done32 = 0;
     const size_t m64 = moments_smem_bytes(ukc_max, 8), m32 = moments_smem_bytes(ukc_max, 4);
-    cudaError_t e = cudaSuccess;
-    if (f64 && m64 > 48 * 1024 && m64 > done64) {
-        e = cudaFuncSetAttribute(k_moments<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m64);
-        if (e == cudaSuccess) done64 = m64;
+    {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        DevAttr* A = nullptr;
+        cudaError_t e = dev_attr(&A);
+        if (e == cudaSuccess && f64 && m64 > 48 * 1024 && m64 > A->mom64) {
+            e = cudaFuncSetAttribute(k_moments<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m64);
+            if (e == cudaSuccess) A->mom64 = m64;
+        }
+        if (e == cudaSuccess && f32 && m32 > 48 * 1024 && m32 > A->mom32) {
+            e = cudaFuncSetAttribute(k_moments<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m32);
+            if (e == cudaSuccess) A->mom32 = m32;
+        }
+        if (e != cudaSuccess) return e;
     }
-    if (e == cudaSuccess && f32 && m32 > 48 * 1024 && m32 > done32) {
-        e = cudaFuncSetAttribute(k_moments<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m32);
-        if (e == cudaSuccess) done32 = m32;
-    }
-    if (e != cudaSuccess) return e;
     dim3 blk(TILE, UPD_WARPS);
     if (f64) k_moments<double><<<n_upd, blk, m64, s>>>(d_inst, d_upd, buf);
     if (f32) k_moments<float><<<n_upd, blk, m32, s>>>(d_inst, d_upd, buf);
@@ -1700,16 +1742,16 @@ cudaError_t launch_resid(const Inst* d_inst, int count, int anchor_inst, double 
     return cudaGetLastError();
 }
 
-static cudaError_t set_smem(size_t smem64, size_t smem32) {
-    static size_t done64 = 0, done32 = 0;
+// (the caller holds g_attr_mu)
+static cudaError_t set_smem(DevAttr* A, size_t smem64, size_t smem32) {
     cudaError_t e = cudaSuccess;
-    if (smem64 > 48 * 1024 && smem64 > done64) {
+    if (smem64 > 48 * 1024 && smem64 > A->upd64) {
         e = cudaFuncSetAttribute(k_update<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
-        if (e == cudaSuccess) done64 = smem64;
+        if (e == cudaSuccess) A->upd64 = smem64;
     }
-    if (e == cudaSuccess && smem32 > 48 * 1024 && smem32 > done32) {
+    if (e == cudaSuccess && smem32 > 48 * 1024 && smem32 > A->upd32) {
         e = cudaFuncSetAttribute(k_update<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
-        if (e == cudaSuccess) done32 = smem32;
+        if (e == cudaSuccess) A->upd32 = smem32;
     }
     return e;
 }
@@ -1722,8 +1764,11 @@ cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int q
 }
 
 cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax) {
-    static bool consts_done = false;
-    if (!consts_done) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    DevAttr* A = nullptr;
+    cudaError_t ed = dev_attr(&A);
+    if (ed != cudaSuccess) return ed;
+    if (!A->consts) {
         float2 h[NINV2];
         h[0] = make_float2(0.0f, 0.0f);
         for (int j = 1; j < NINV2; ++j) {
@@ -1731,34 +1776,37 @@ cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax) {
             const float hi = (float)v;
             h[j] = make_float2(hi, (float)(v - (double)hi));
         }
+        // synchronous copy: the table is in place before any kernel of this device uses it
         cudaError_t e = cudaMemcpyToSymbol(c_inv2, h, sizeof(h));
         if (e != cudaSuccess) return e;
-        consts_done = true;
+        A->consts = true;
     }
-    static int nodal_done = 0;
     const int smem = nodal_smem_doubles(qmax) * (int)sizeof(double);
-    if (smem > 48 * 1024 && smem > nodal_done) {
+    if (smem > 48 * 1024 && smem > A->nodal) {
         cudaError_t e = cudaFuncSetAttribute(k_nodal<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_nodal<QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        nodal_done = smem;
+        A->nodal = smem;
     }
-    return set_smem(smem64, smem32);
+    return set_smem(A, smem64, smem32);
 }
 
-// Attributes only ever grow, so that contexts created earlier keep launching.
+// Attributes only ever grow, so that contexts created earlier keep launching; slot 0 records
+// k_resident<8>, slot 1 k_resident<QMAX>.
 template <int QB>
 static cudaError_t resident_config(size_t smem, int cs) {
-    static size_t smem_done = 0;
-    static bool nonportable = false;
-    cudaError_t e = cudaSuccess;
-    if (smem > smem_done) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    DevAttr* A = nullptr;
+    cudaError_t e = dev_attr(&A);
+    if (e != cudaSuccess) return e;
+    const int slot = QB == 8 ? 0 : 1;
+    if (smem > A->res[slot]) {
         e = cudaFuncSetAttribute(k_resident<QB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) smem_done = smem;
+        if (e == cudaSuccess) A->res[slot] = smem;
     }
-    if (e == cudaSuccess && cs > 8 && !nonportable) {
+    if (e == cudaSuccess && cs > 8 && !A->nonport[slot]) {
         e = cudaFuncSetAttribute(k_resident<QB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e == cudaSuccess) nonportable = true;
+        if (e == cudaSuccess) A->nonport[slot] = true;
     }
     return e;
 }

@@ -74,6 +74,7 @@ extern "C" int fdlb_step_noalloc(const fdlb_params* params, void* dev_f, size_t 
     rc = fdlb_create(&c, params, 1, ws, FDLB_NOALLOC_SCRATCH_BYTES, stream);
     if (rc) return rc;
     fdlb_set_schedule(c, FDLB_SCHED_TILED);
+    fdlb::ctx_direct_launches(c);
     cudaStream_t s = fdlb::ctx_stream(c);
     void* F = nullptr;
     size_t fb = 0;

@@ -99,6 +99,7 @@ def load() -> C.CDLL:
         "fdlb_create": (C.c_int, [C.POINTER(vp), P, C.c_int32, vp, C.c_size_t, vp]),
         "fdlb_destroy": (None, [vp]),
         "fdlb_info": (C.c_int, [vp, C.c_int32, ip, ip, dp]),
+        "fdlb_layout": (C.c_int, [vp, C.c_int32, ip, ip, ip]),
         "fdlb_step": (C.c_int, [vp, C.c_int64, C.c_double]),
         "fdlb_run": (C.c_int, [vp, C.c_double, C.c_int64, C.c_int64, C.c_double]),
         "fdlb_moments": (C.c_int, [vp, C.c_int32, dp]),
@@ -154,17 +155,50 @@ def quadrature(kind: str, q: int):
     return x, w
 
 
+def noalloc_f_elements(params: Params) -> int:
+    """Values of f of one instance in the layout of include/fdlb.h: K x ceil(nx/32)*32."""
+    tc = params.qy * params.qz if params.qz else (2 * params.qy if params.qy else 2)
+    return 2 * params.qx_half * tc * ((params.nx + 31) // 32 * 32)
+
+
 def step_noalloc(params: Params, f_dev, nsteps: int, moments_dev=None, stream=None) -> None:
     """fdlb_step_noalloc: advance one instance whose f lives in the caller's device tensor
     f_dev (in place), with no device allocation by the library; moments_dev (float64 device
-    tensor of 8*nx) receives the moment rows."""
+    tensor of at least 8*nx values on f_dev's device) receives the moment rows.
+
+    The buffers are checked here before the library sees their addresses: f_dev must be a
+    contiguous tensor of float64 (precision "fp64") or float32 (precision "fp32") holding
+    exactly the instance's f; moments_dev must be contiguous float64 with numel >= 8*nx on
+    the same CUDA device.  A violation raises ValueError and launches nothing."""
     import torch
+    want = {"fp64": torch.float64, "fp32": torch.float32}.get(params.precision)
+    if want is None:
+        raise ValueError(f"step_noalloc: precision {params.precision!r} is not supported (fp64 or fp32)")
+    if f_dev.dtype != want:
+        raise ValueError(f"step_noalloc: f_dev is {f_dev.dtype}, precision {params.precision!r} needs {want}")
+    if not f_dev.is_contiguous():
+        raise ValueError("step_noalloc: f_dev must be contiguous")
+    nf = noalloc_f_elements(params)
+    if f_dev.numel() != nf:
+        raise ValueError(f"step_noalloc: f_dev has {f_dev.numel()} values, this instance's f has {nf}")
+    if moments_dev is not None:
+        if moments_dev.dtype != torch.float64:
+            raise ValueError(f"step_noalloc: moments_dev is {moments_dev.dtype}, needs torch.float64")
+        if not moments_dev.is_contiguous():
+            raise ValueError("step_noalloc: moments_dev must be contiguous")
+        if moments_dev.numel() < 8 * params.nx:
+            raise ValueError(f"step_noalloc: moments_dev has {moments_dev.numel()} values, needs {8 * params.nx}")
+        if moments_dev.device != f_dev.device:
+            raise ValueError(f"step_noalloc: moments_dev is on {moments_dev.device}, f_dev on {f_dev.device}")
+    if f_dev.device.type != "cuda":
+        raise ValueError(f"step_noalloc: f_dev must be a CUDA tensor, not on {f_dev.device}")
     lib = load()
     c = params.to_c()
     st = stream if stream is not None else torch.cuda.current_stream(f_dev.device)
     mp = C.cast(C.c_void_p(moments_dev.data_ptr()), C.POINTER(C.c_double)) if moments_dev is not None else None
-    rc = lib.fdlb_step_noalloc(C.byref(c), C.c_void_p(f_dev.data_ptr()), f_dev.numel() * f_dev.element_size(),
-                               int(nsteps), mp, C.c_void_p(st.cuda_stream))
+    with torch.cuda.device(f_dev.device):
+        rc = lib.fdlb_step_noalloc(C.byref(c), C.c_void_p(f_dev.data_ptr()), f_dev.numel() * f_dev.element_size(),
+                                   int(nsteps), mp, C.c_void_p(st.cuda_stream))
     if rc != FDLB_OK:
         raise FdlbError(rc, lib.fdlb_last_error(None).decode())
 
@@ -255,6 +289,12 @@ class Solver:
         r = np.zeros(self.count)
         self._check(self.lib.fdlb_residual(self.ctx, _dptr(r)))
         return r
+
+    def layout(self, inst: int = 0):
+        """(velocities per update block, update blocks per 32-node tile, tiles) of instance inst."""
+        ch, g, t = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(self.lib.fdlb_layout(self.ctx, inst, C.byref(ch), C.byref(g), C.byref(t)))
+        return ch.value, g.value, t.value
 
     def set_schedule(self, schedule: str):
         """'auto' (time both on the first long step call), 'tiled' or 'resident'."""

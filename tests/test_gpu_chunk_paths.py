@@ -1,0 +1,69 @@
+"""FP64 oracle parity of the bench's own instance on each velocity-chunk path of the tiled
+update kernel.  The batch size decides how a tile's velocities are split over update blocks
+(16 per block below 38 tiles, 32 up to 1215 tiles, the whole set -- at most 256 -- from 1216
+tiles on) and with it the order in which the blocks' partial moment sums are added, so each
+path is checked on its own.  The instance is the Couette set-up of Sec. IV as the sweep
+uses it: Nx = 200 tanh-stretched nodes (A = 1.5), walls at T = 1 moving at u_y = -+0.42,
+eta0 = 0.1, Kn = 0.5, 12 x 6 x 4 = 288 velocities.  Padding instances (cheap 1D reduced
+Fourier problems) only set the batch size."""
+import numpy as np
+import pytest
+
+from gpu_common import compare, lib, oracle_for
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 200
+BENCH = dict(nx=200, qx_half=6, qy=6, qz=4, kn=0.5, eta0=0.1, U_left=-0.42, U_right=0.42, grid="tanh", stretch=1.5)
+PAD = dict(qx_half=1, qy=0, qz=0, kn=0.2, eta0=0.05, T_left=0.98, T_right=1.02)
+
+
+@pytest.fixture(scope="module")
+def oracle_moments():
+    F = lib()
+    o = oracle_for(F.Params(**BENCH))
+    o.step(STEPS)
+    return o.moments()
+
+
+def batch(F, pad_tiles, precision):
+    ps = [F.Params(**BENCH, precision=precision)]
+    while pad_tiles > 0:
+        nx = min(512, 32 * pad_tiles)
+        ps.append(F.Params(nx=nx, **PAD, precision=precision))
+        pad_tiles -= nx // 32
+    return ps
+
+
+@pytest.mark.parametrize("pad_tiles,chunk,groups", [(0, 16, 18), (32, 32, 9), (1216, 256, 2)])
+def test_bench_instance_fp64_each_chunk_path(oracle_moments, pad_tiles, chunk, groups):
+    F = lib()
+    s = F.Solver(batch(F, pad_tiles, "fp64"))
+    s.set_schedule("tiled")
+    assert s.layout(0) == (chunk, groups, 7)
+    s.step(STEPS)
+    r, st, nst = s.status()
+    assert st[0] == F.ACTIVE and nst[0] == STEPS
+    compare(s.moments(0), oracle_moments, 1e-12, f"chunk {chunk}")
+
+
+def test_bench_instance_fp32_chunk32(oracle_moments):
+    """The bench's configuration: FP32 storage, 32-velocity chunks."""
+    F = lib()
+    s = F.Solver(batch(F, 32, "fp32"))
+    assert s.layout(0)[0] == 32
+    s.step(STEPS)
+    compare(s.moments(0), oracle_moments, 1e-5, "fp32 chunk 32")
+
+
+def test_chunk_paths_agree_bitwise_on_padding_instance():
+    """The arithmetic of a padding instance's moments is the same on every path up to the
+    chunk partial-sum order; its 1D reduced set has 4 velocities, one chunk on all paths,
+    so its results agree bitwise."""
+    F = lib()
+    outs = []
+    for pad in (32, 1216):
+        s = F.Solver(batch(F, pad, "fp64"))
+        s.step(20)
+        outs.append(s.moments(1)["T"])
+    assert np.array_equal(outs[0], outs[1])

@@ -7,7 +7,7 @@ Collected last on purpose (file name), so a stop-at-first-failure run has run al
 import numpy as np
 import pytest
 
-from gpu_common import lib
+from gpu_common import compare, lib, oracle_for
 
 pytestmark = pytest.mark.gpu
 
@@ -31,17 +31,25 @@ def test_step_noalloc_matches_context_path_twice():
             assert np.max(np.abs(got[j] - M[k]) / scale) <= 1e-12, (call, k)
         fr = np.frombuffer(ref.get_state(0), dtype=np.float64, offset=24)
         assert np.max(np.abs(f_dev.cpu().numpy() - fr)) <= 1e-12 * np.max(np.abs(fr)), call
+    # and both against the oracle after the 80 steps of the two calls
+    o = oracle_for(p)
+    o.step(80)
+    got = mom.cpu().numpy().reshape(8, p.nx)
+    compare({k: got[j] for j, k in enumerate(F.MOMENT_ROWS)}, o.moments(), 1e-12, "step_noalloc vs oracle")
 
 
 def test_step_noalloc_rejects_oversize_and_bad_buffer():
+    """The library's own checks, called through the C ABI directly (the binding's checks
+    would stop these buffers before the library sees them)."""
+    import ctypes
     import torch
     F = lib()
-    big = F.Params(nx=4096, qx_half=16, qy=8, qz=8, kn=0.1, eta0=0.1)
+    L = F.load()
     f_dev = torch.zeros(16, dtype=torch.float64, device="cuda")
-    with pytest.raises(F.FdlbError) as e:
-        F.step_noalloc(big, f_dev, 1)
-    assert e.value.code == F.FDLB_ENOMEM and "static maximum" in str(e.value)
-    p = F.Params(nx=16, qx_half=4, qy=4, qz=0, kn=0.1, eta0=0.1)
-    with pytest.raises(F.FdlbError) as e:
-        F.step_noalloc(p, f_dev, 1)
-    assert e.value.code == F.FDLB_EINVAL
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    big = F.Params(nx=4096, qx_half=16, qy=8, qz=8, kn=0.1, eta0=0.1).to_c()
+    rc = L.fdlb_step_noalloc(ctypes.byref(big), ctypes.c_void_p(f_dev.data_ptr()), 16 * 8, 1, None, st)
+    assert rc == F.FDLB_ENOMEM and "static maximum" in L.fdlb_last_error(None).decode()
+    p = F.Params(nx=16, qx_half=4, qy=4, qz=0, kn=0.1, eta0=0.1).to_c()
+    rc = L.fdlb_step_noalloc(ctypes.byref(p), ctypes.c_void_p(f_dev.data_ptr()), 16 * 8, 1, None, st)
+    assert rc == F.FDLB_EINVAL and "f_bytes" in L.fdlb_last_error(None).decode()
