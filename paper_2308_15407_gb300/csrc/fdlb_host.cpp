@@ -379,6 +379,28 @@ struct Layout {
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
+}  // namespace
+
+// FNV-1a over the fields of a parameter set (field by field, so that struct padding never
+// enters).  fp32_alike: FDLB_FP32_STORAGE and FDLB_FP32_THEN_FP64 hash alike (the stochastic
+// rounding seed, so that both round identically while both store FP32).
+static uint64_t params_fnv(const fdlb_params& p, bool fp32_alike) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* v, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(v);
+        for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    };
+    int32_t prec = p.precision;
+    if (fp32_alike && prec == FDLB_FP32_THEN_FP64) prec = FDLB_FP32_STORAGE;
+    const int32_t iv[] = {p.flow, p.nx, p.grid, p.qx_half, p.qy, p.qz, prec, p.j1_shear, p.chi_model, p.x_quadrature};
+    const double dv[] = {p.stretch, p.kn, p.eta0, p.T_left, p.T_right, p.U_left, p.U_right, p.accel_y, p.cfl, p.dt, p.T_init};
+    mix(iv, sizeof(iv));
+    mix(dv, sizeof(dv));
+    return h;
+}
+
+namespace {
+
 // Velocities per update block: small batches split a tile's velocities into chunks (16 for
 // fewer than 38 tiles, a quarter of the SMs; 32 up to 1216 tiles) to occupy the GPU; large
 // batches give a block the whole tile (the node table is loaded once), at most 256
@@ -532,6 +554,10 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         I.two_phase = p.precision == FDLB_FP32_THEN_FP64;
         I.j1_shear = p.j1_shear;
         I.chi_model = p.chi_model; I.ntab = L.ntab; I.mgroups = L.groups; I.ukc = L.ukc;
+        {
+            const uint64_t h = params_fnv(p, true);
+            I.sr_key = (uint32_t)(h ^ (h >> 32));
+        }
         const bool xfull = p.x_quadrature == FDLB_XQ_FULL;
         const int Lx = xfull ? 2 * Q : Q;
         I.xfull = xfull; I.Lx = Lx;
@@ -1091,12 +1117,7 @@ extern "C" int fdlb_set_profiles(fdlb_ctx* c, int32_t inst, const double* n, con
 }
 
 // ---- checkpoint: [magic u64][hash u64][steps i64][f bytes]
-static uint64_t param_hash(const fdlb_params& p) {
-    const unsigned char* b = reinterpret_cast<const unsigned char*>(&p);
-    uint64_t h = 1469598103934665603ull;
-    for (size_t i = 0; i < sizeof(p); ++i) { h ^= b[i]; h *= 1099511628211ull; }
-    return h;
-}
+static uint64_t param_hash(const fdlb_params& p) { return params_fnv(p, false); }
 
 // Two-phase instances add [storage i64][switch step i64] after the header and always carry f
 // at its FP64 size.

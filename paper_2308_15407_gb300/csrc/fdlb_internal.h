@@ -49,6 +49,7 @@ struct Inst {
     int Lx;                    // orthonormal x polynomials in the projection: Q (half), 2Q (full)
     int two_phase;             // FDLB_FP32_THEN_FP64: tables and buffers exist for both storages
     int ntab;                  // doubles per node in the projection table
+    uint32_t sr_key;           // hash of the parameters: seeds the stochastic rounding of FP32 storage
     int ukc;                   // velocities per update block (chunk) of a tile
     int mgroups;               // update chunks per tile (> 1: partial moment sums in msum)
     double kn, eta0, chi0, mu0c, dt, ds, accel_y;

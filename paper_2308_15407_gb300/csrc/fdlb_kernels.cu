@@ -1259,6 +1259,49 @@ __device__ __forceinline__ float weno_face(float a, float b, float c, float d, f
 
 constexpr int UPD_WARPS = 8;
 
+// ---------------------------------------------------------------------------
+// stochastic rounding of FP32 storage
+// ---------------------------------------------------------------------------
+// With round-to-nearest, FP32 storage drops every per-step change below half an ulp of f, so a
+// solve stalls at a distance ~ ulp / (2 eps) from the steady state (eps = decay per step of its
+// slowest mode; ~5e-5 on the Couette sweep), and the dropped changes no longer sum to zero
+// over the channel, which drifts the mass.  Rounding base + inc up or down at random, with the
+// probabilities that make the expected stored value the exact sum (Connolly, Higham & Mary,
+// SIAM J. Sci. Comput. 43, 2021), keeps small changes in expectation: no stall, and a mass
+// error that only random-walks.  The random bits come from a counter-based hash of (the
+// instance's parameters, step, stage, velocity, node), so runs are reproducible, both schedules
+// round alike, and an instance rounds the same way whatever batch it is in.
+
+// MurmurHash3's 32-bit finalizer (Appleby, public domain): a bijective avalanche mix.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Per-launch seed of instance I for RK stage `stage` of the current step.
+__device__ __forceinline__ uint32_t sr_seed(const Inst& I, int stage) {
+    const unsigned long long step = (unsigned long long)*(volatile long long*)I.steps;
+    return fmix32((uint32_t)(step * 3ull + (unsigned long long)stage) ^ fmix32(I.sr_key));
+}
+
+// base + inc stored as a float: the exact sum s + err (TwoSum) goes to its round-to-nearest
+// value s, or to the neighbouring float on the side of err with probability |err| / gap, so
+// that its expectation is the exact sum.
+__device__ __forceinline__ float sr_add(float base, float inc, uint32_t bits) {
+    const float s = __fadd_rn(base, inc);
+    const float bb = __fsub_rn(s, base);
+    const float err = __fadd_rn(__fsub_rn(base, __fsub_rn(s, bb)), __fsub_rn(inc, bb));
+    if (err == 0.0f) return s;
+    const float nb = nextafterf(s, err > 0.0f ? CUDART_INF_F : -CUDART_INF_F);
+    const float gap = fabsf(__fsub_rn(nb, s));
+    const float u = __uint2float_rz(bits >> 8) * 0x1p-24f;        // uniform on [0, 1), exact
+    return __fmul_rn(u, gap) < fabsf(err) ? nb : s;
+}
+
 // Tables read by the update kernel in its compute type (FP32 copies for FP32 storage).
 template <typename C>
 struct Tabs;
@@ -1448,6 +1491,7 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const C ca = stage == 1 ? (C)0 : (stage == 2 ? (C)0.75 : (C)(1.0 / 3.0));
     const C cb = stage == 1 ? (C)1 : (stage == 2 ? (C)0.25 : (C)(2.0 / 3.0));
     const C dt = (C)I.dt;
+    const uint32_t seed = sizeof(S) == 4 ? sr_seed(I, stage) : 0u;
     const C nwL = (C)I.misc[M_NWL], nwR = (C)I.misc[M_NWR];
     const C xpi = valid ? Tabs<C>::xpinv(I)[i] : (C)0;
     const C invtau = stab[(8 * Q + 4 * Tc) * TILE + lane];
@@ -1542,8 +1586,10 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
             // (stage 1: f + dt L).  In the printed form ca F + cb (f + dt L) the rounded
             // weights (float) 1/3 + (float) 2/3 = 1 + 3e-8 scale a steady f up by half an ulp
             // every step, a mass drift of ~1e-3 over a solve; the increment form has no such
-            // bias and leaves f unchanged where the update vanishes.
-            out = stage == 1 ? fi + dt * L : Fk + cb * ((fi - Fk) + dt * L);
+            // bias.  The sum is stored with stochastic rounding (sr_add).
+            const C base = stage == 1 ? fi : Fk;
+            const C inc = stage == 1 ? dt * L : cb * ((fi - Fk) + dt * L);
+            out = sr_add(base, inc, fmix32(((uint32_t)k * (uint32_t)ld + (uint32_t)i) ^ seed));
         } else {
             out = cb * (fi + dt * L);
             if (stage != 1) out += ca * Fk;

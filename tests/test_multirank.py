@@ -61,7 +61,7 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch):
     import bench
     monkeypatch.setenv("RANK", "1")
     called = []
-    monkeypatch.setattr(bench, "oracle_rate", lambda **kw: called.append(kw))
+    monkeypatch.setattr(bench, "oracle_pool_rate", lambda **kw: called.append(kw))
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(type("A", (), dict(steps=3, warmup=3, gpus=2))())
