@@ -581,8 +581,9 @@ def run_fdlb(args):
 
 def run_profile_case(case, precision):
     """Small fixed workloads for ncu captures (no timing, no JSON line).
-    couette1 / couette12: one instance (eta0 = 0.2, Kn = 0.5) or the whole Couette sweep, tiled
-    schedule: creation (5 launches), 20 steps (7 launches each), 3 more steps.
+    couette1 / couette12: one instance (eta0 = 0.2, Kn = 0.5) or the whole Couette sweep;
+    sweep2048: the 2048-instance mixed sweep (f 162 MB in FP32); tiled schedule: creation
+    (5 launches), 20 steps (7 launches each), 3 more steps.
     mlp: the warm-start network on 32768 points, 6 training steps and one prediction."""
     import torch
     from paper_2308_15407_gb300 import fdlb as F
@@ -601,7 +602,11 @@ def run_profile_case(case, precision):
         torch.cuda.synchronize()
         print("ok")
         return
-    ps = couette_params(F, precision)
+    if case == "sweep2048":
+        from paper_2308_15407_gb300 import workloads
+        ps = [F.Params(**d) for d in workloads.batched_sweep(precision=precision)]
+    else:
+        ps = couette_params(F, precision)
     if case == "couette1":
         ps = ps[4:5]
     s = F.Solver(ps)
@@ -619,7 +624,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fdlb", choices=["fdlb", "reference"])
-    ap.add_argument("--profile-case", choices=["couette1", "couette12", "mlp"], default=None,
+    ap.add_argument("--profile-case", choices=["couette1", "couette12", "sweep2048", "mlp"], default=None,
                     help="run a small fixed workload for an ncu capture instead of the benchmark")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()

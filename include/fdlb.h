@@ -114,6 +114,9 @@ extern "C" {
 #define FDLB_FAILED_UNPHYSICAL 3
 #define FDLB_STAGNATED     4   /* FDLB_FP32_STORAGE stepped with freeze_tol > 0: f stopped changing
                                   (residual exactly 0) before the residual reached freeze_tol */
+#define FDLB_FAILED_COPY   5   /* an asynchronous copy into shared memory did not complete within the
+                                  kernel's wait limit (~2 s); the instance is no longer advanced and
+                                  fdlb_run reports FDLB_ETIMEOUT */
 
 /* Parameters of one channel problem.  Set struct_size = sizeof(fdlb_params). */
 typedef struct fdlb_params {

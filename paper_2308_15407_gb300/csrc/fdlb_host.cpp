@@ -406,6 +406,7 @@ namespace {
 // batches give a block the whole tile (the node table is loaded once), at most 256
 // velocities (the block keeps its outputs in shared memory for the moments).
 constexpr int UKC_MAX = 256;
+constexpr size_t UPD_SMEM_LIMIT = 220 * 1024;   // dynamic shared memory of one update block, at most
 int upd_chunk(const std::vector<fdlb_params>& ps) {
     long tiles = 0;
     for (auto& p : ps) tiles += (p.nx + TILE - 1) / TILE;
@@ -459,6 +460,12 @@ Layout layout_of(const fdlb_params& p, int ukc) {
     L.misc = al256(8 * 8);
     L.tab32 = f32 ? al256((size_t)L.ntab * L.ld * 4) : 0;
     L.ukc = std::min(L.K, ukc);
+    // the update block stages its chunk's rows in shared memory: halve the chunk of the largest
+    // velocity sets until a block fits in the per-block limit (with room for the static part)
+    {
+        const size_t s_max = p.precision == FDLB_FP32_STORAGE ? 4 : 8;
+        while (L.ukc > 8 && update_smem_bytes(L.ntab, L.ukc, s_max, s_max) > UPD_SMEM_LIMIT) L.ukc = (L.ukc + 1) / 2;
+    }
     L.groups = (L.K + L.ukc - 1) / L.ukc;
     L.msum = L.groups > 1 ? al256((size_t)L.groups * MOM_SUMS * L.ld * 8) : 0;
     L.mcnt = al256((size_t)(L.ld / TILE) * 4);
@@ -1064,13 +1071,15 @@ extern "C" int fdlb_run(fdlb_ctx* c, double tol, int64_t max_steps, int64_t chec
     while (true) {
         int rc = fdlb_status(c, nullptr, st.data(), nullptr);
         if (rc) return rc;
-        bool active = false, nonfinite = false, unphys = false, stagnated = false;
+        bool active = false, nonfinite = false, unphys = false, stagnated = false, copy = false;
         for (int s : st) {
             active |= s == FDLB_ACTIVE;
             nonfinite |= s == FDLB_FAILED_NONFINITE;
             unphys |= s == FDLB_FAILED_UNPHYSICAL;
             stagnated |= s == FDLB_STAGNATED;
+            copy |= s == FDLB_FAILED_COPY;
         }
+        if (copy) return fail(c, FDLB_ETIMEOUT, "an asynchronous copy into shared memory did not complete (FDLB_FAILED_COPY)");
         if (!active || done >= max_steps) {
             if (nonfinite) return fail(c, FDLB_ENONFINITE, "an instance produced a non-finite moment");
             if (unphys) return fail(c, FDLB_EUNPHYSICAL, "an instance produced n <= 0 or T <= 0");

@@ -356,6 +356,15 @@ struct InnerSum<float> {
         hi = t;
         lo += err + e;
     }
+    // adds a value known exactly (a product by a power of two), TwoSum on the head: the same
+    // result as add() with a zero product error
+    __device__ __forceinline__ void add_exact(float p) {
+        const float t = hi + p;
+        const float bb = t - hi;
+        const float err = (hi - (t - bb)) + (p - bb);
+        hi = t;
+        lo += err;
+    }
     // adds another pair's value h + l (TwoSum on the heads)
     __device__ __forceinline__ void add_pair(float h, float l) {
         const float t = hi + h;
@@ -1240,20 +1249,30 @@ __device__ __forceinline__ float weno_face(float a, float b, float c, float d, f
     const float s1 = fmaf(13.0f / 12.0f, t1 * t1, 0.25f * t2 * t2);
     const float s2 = fmaf(13.0f / 12.0f, u1 * u1, 0.25f * u2 * u2);
     const float s3 = fmaf(13.0f / 12.0f, v1 * v1, 0.25f * v2 * v2);
-    const float smin = fminf(s1, fminf(s2, s3));
+    const float smax = fmaxf(s1, fmaxf(s2, s3));
     float w1, w2, w3;
-    if (smin == 0.0f) {
-        w1 = s1 == 0.0f ? 0.1f : 0.0f;
-        w2 = s2 == 0.0f ? 0.6f : 0.0f;
-        w3 = s3 == 0.0f ? 0.3f : 0.0f;
+    if (smax < 1e-30f) {
+        // uniform to FP32 resolution (indicators zero or below any meaningful difference): the
+        // candidates agree, the ideal weights are the limit
+        w1 = 0.1f; w2 = 0.6f; w3 = 0.3f;
     } else {
-        // delta_q (phi_min/phi_q)^2: no overflow or underflow of the sum
-        const float r1 = smin / s1, r2 = smin / s2, r3 = smin / s3;
-        w1 = 0.1f * r1 * r1;
-        w2 = 0.6f * r2 * r2;
-        w3 = 0.3f * r3 * r3;
+        // omega_q ~ delta_q / phi_q^2 ~ delta_q prod_{r != q} phi_r^2, phi scaled by the largest
+        // (one reciprocal; fast division: the FP32 form's tolerance is far above its error)
+        const float r = __fdividef(1.0f, smax);
+        const float a1 = s1 * r, a2 = s2 * r, a3 = s3 * r;
+        const float p1 = a1 * a1, p2 = a2 * a2, p3 = a3 * a3;
+        w1 = 0.1f * p2 * p3;
+        w2 = 0.6f * p1 * p3;
+        w3 = 0.3f * p1 * p2;
+        if (w1 + w2 + w3 < 1e-30f) {
+            // two indicators vanish relative to the third (or underflow): weight on the smallest
+            const float smin = fminf(s1, fminf(s2, s3));
+            w1 = s1 == smin ? 0.1f : 0.0f;
+            w2 = s2 == smin ? 0.6f : 0.0f;
+            w3 = s3 == smin ? 0.3f : 0.0f;
+        }
     }
-    const float is = 1.0f / (w1 + w2 + w3);
+    const float is = __fdividef(1.0f, w1 + w2 + w3);
     return fmaf(w1 * is, F1, fmaf(w2 * is, F2, w3 * is * F3));
 }
 
@@ -1296,7 +1315,12 @@ __device__ __forceinline__ float sr_add(float base, float inc, uint32_t bits) {
     const float bb = __fsub_rn(s, base);
     const float err = __fadd_rn(__fsub_rn(base, __fsub_rn(s, bb)), __fsub_rn(inc, bb));
     if (err == 0.0f) return s;
-    const float nb = nextafterf(s, err > 0.0f ? CUDART_INF_F : -CUDART_INF_F);
+    // the neighbouring float on the side of err: one unit in the last place of s's magnitude
+    // bits, up when s and err have the same sign, down otherwise (s = 0: the smallest
+    // subnormal with err's sign)
+    const uint32_t sb = __float_as_uint(s);
+    const float nb = s == 0.0f ? copysignf(__uint_as_float(1u), err)
+                               : __uint_as_float((s > 0.0f) == (err > 0.0f) ? sb + 1u : sb - 1u);
     const float gap = fabsf(__fsub_rn(nb, s));
     const float u = __uint2float_rz(bits >> 8) * 0x1p-24f;        // uniform on [0, 1), exact
     return __fmul_rn(u, gap) < fabsf(err) ? nb : s;
@@ -1324,12 +1348,24 @@ struct Tabs<float> {
     __device__ static const float* Ky(const Inst& I) { return I.Ky32; }
 };
 
-// Shared memory of one update item: table, transverse moment weights, the chunk's outputs,
-// per-warp moment sums, sums.
+// Shared memory of one update item: the projection table, the transverse moment weights, the
+// staged source rows of the chunk (each with a 4-node halo on either side: 40 values per row;
+// the epilogue's per-warp sums reuse this space once the rows are consumed), and the step's F
+// values, which the outputs replace (the epilogue reads them there).
 constexpr size_t TW_BYTES = (size_t)NTW * TCMAX * sizeof(double);
+constexpr int SW = 40;                // staged row: nodes i0 - 4 .. i0 + 35
 __host__ __device__ inline size_t upd_table_bytes(int ntab, size_t c) { return ((size_t)ntab * TILE * c + 15) / 16 * 16; }
+__host__ __device__ inline size_t upd_ex_bytes() { return (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double); }
+__host__ __device__ inline size_t upd_stage_bytes(int ukc, size_t s) {
+    const size_t rows = (size_t)ukc * SW * s, ex = upd_ex_bytes();
+    return ((rows > ex ? rows : ex) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t upd_stage_offset(int ntab, size_t c) { return upd_table_bytes(ntab, c) + TW_BYTES; }
+__host__ __device__ inline size_t upd_fo_offset(int ntab, int ukc, size_t c, size_t s) {
+    return upd_stage_offset(ntab, c) + upd_stage_bytes(ukc, s);
+}
 __host__ __device__ inline size_t upd_smem_bytes(int ntab, int ukc, size_t c, size_t s) {
-    return upd_table_bytes(ntab, c) + TW_BYTES + (size_t)ukc * TILE * s + (size_t)(UPD_WARPS + 1) * MOM_SUMS * TILE * sizeof(double);
+    return upd_fo_offset(ntab, ukc, c, s) + (size_t)ukc * TILE * s;
 }
 
 // Transverse moment weights of the epilogue into shared memory (FP32 storage: float heads
@@ -1375,7 +1411,15 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
             for (int t = ta; t < tb; ++t) {
                 const float fv = fo[(kx * Tc + t - k0) * TILE + lane];
 #pragma unroll
-                for (int j = 0; j < NTW; ++j) a[j].add(fv, 0.0, twh[j * Tc + t], twl[j * Tc + t]);
+                for (int j = 0; j < NTW; ++j) {
+                    // the weight is the same for every lane: zero weights (the mass and energy
+                    // flags of the reduced slots) are skipped, power-of-two weights with no
+                    // tail give exact products; both leave the sum's bits as add() would
+                    const float wh = twh[j * Tc + t], wl = twl[j * Tc + t];
+                    if (wh == 0.0f) continue;
+                    if (wl == 0.0f && (__float_as_uint(wh) & 0x007fffffu) == 0u) a[j].add_exact(fv * wh);
+                    else a[j].add(fv, 0.0, wh, wl);
+                }
             }
             df Sd[NTW];
 #pragma unroll
@@ -1407,7 +1451,10 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
             for (int t = ta; t < tb; ++t) {
                 const double fv = fo[(kx * Tc + t - k0) * TILE + lane];
 #pragma unroll
-                for (int j = 0; j < NTW; ++j) a[j].add(fv, tw[j * Tc + t], 0.0f, 0.0f);
+                for (int j = 0; j < NTW; ++j) {
+                    const double w = tw[j * Tc + t];
+                    if (w != 0.0) a[j].add(fv, w, 0.0f, 0.0f);     // same for every lane
+                }
             }
             double Sv[NTW];
 #pragma unroll
@@ -1450,15 +1497,103 @@ __device__ void chunk_ticket_final(const Inst& I, int i0, double* ss) {
     moments_final_tile<S>(I, i0, ss, tid, UPD_WARPS, 1);
 }
 
+// ---- bulk asynchronous copies into shared memory (cp.async.bulk with an mbarrier) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bytes (a multiple of 16) from global src to shared dst (both 16-byte aligned), completing on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// Phase `parity` of bar complete?  Each poll may suspend the thread for up to ~1 us.
+__device__ __forceinline__ bool mbar_poll(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+constexpr long COPY_WAIT_POLLS = 2000000;      // ~2 s at the suspend hint
+
+// Rows [k0, k0 + nrows) of one tile into shared memory: the source stage's values of nodes
+// i0 - 4 .. i0 + 35 (clipped to the row) into Sw[r][0..SW), and, with F, the step's values of
+// nodes i0 .. i0 + 31 into Fo[r][0..TILE).  BULK: one cp.async.bulk per row, all of the block's
+// rows in flight at once, completion counted in bytes on an mbarrier (the tiled schedule);
+// otherwise plain loads (the resident schedule).  Both leave the same values in shared memory.
+// Window bounds are multiples of 4 nodes, so every bulk copy starts on a 16-byte boundary and
+// moves a multiple of 16 bytes.  Returns false if the copies did not complete within the wait
+// limit (the instance is then marked FDLB_FAILED_COPY).
+template <typename S, bool BULK>
+__device__ bool stage_rows(const Inst& I, int i0, int k0, int nrows, int stage, S* Sw, S* Fo, int lane, int wy) {
+    const int ld = I.ld;
+    const int lo = max(0, i0 - 4), hi = min(ld, i0 + 36);
+    const int off = lo - (i0 - 4);
+    const S* src = static_cast<const S*>(I.f[stage - 1]);
+    const S* F = static_cast<const S*>(I.f[0]);
+    const bool withF = stage != 1;
+    if constexpr (BULK) {
+        __shared__ __align__(8) uint64_t bar;
+        const uint32_t rowbytes = (uint32_t)(hi - lo) * sizeof(S), fbytes = TILE * sizeof(S);
+        const int tid = wy * TILE + lane;
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            mbar_expect_tx(&bar, (uint32_t)nrows * (rowbytes + (withF ? fbytes : 0u)));
+        }
+        // earlier generic accesses of this shared memory come before the copies' writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (lane == 0)
+            for (int r = wy; r < nrows; r += UPD_WARPS) {
+                bulk_g2s(Sw + r * SW + off, src + (size_t)(k0 + r) * ld + lo, rowbytes, &bar);
+                if (withF) bulk_g2s(Fo + r * TILE, F + (size_t)(k0 + r) * ld + i0, fbytes, &bar);
+            }
+        bool ok = false;
+        for (long it = 0; it < COPY_WAIT_POLLS && !ok; ++it) ok = mbar_poll(&bar, 0);
+        if (__syncthreads_or(!ok)) {          // the same decision in every thread of the block
+            if (tid == 0) atomicExch(I.status, FDLB_FAILED_COPY);
+            // give copies still in flight a second bounded wait before the block leaves
+            for (long it = 0; it < COPY_WAIT_POLLS && !mbar_poll(&bar, 0); ++it) {
+            }
+            __syncthreads();
+            return false;
+        }
+        if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(&bar)) : "memory");
+        return true;
+    } else {
+        __syncthreads();
+        const int n = hi - lo;
+        for (int r = wy; r < nrows; r += UPD_WARPS) {
+            const S* row = src + (size_t)(k0 + r) * ld + lo;
+            for (int j = lane; j < n; j += TILE) Sw[r * SW + off + j] = row[j];
+            if (withF) Fo[r * TILE + lane] = F[(size_t)(k0 + r) * ld + i0 + lane];
+        }
+        __syncthreads();
+        return true;
+    }
+}
+
 // Velocities [k0, k1) of one tile for RK stage `stage`, by UPD_WARPS warps (lane, warp wy);
-// smem_raw holds upd_smem_bytes(ntab, ukc, sizeof(C), sizeof(S)).  The epilogue computes the
-// moments of the new values (chunk_moments).
-template <typename S, typename C>
-__device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, unsigned char* smem_raw, int lane, int wy) {
+// smem_raw holds upd_smem_bytes(ntab, ukc, sizeof(C), sizeof(S)).  The chunk's source rows (and
+// F) are staged in shared memory first (stage_rows); the stencil, the ghost cells of the diffuse
+// walls and F are then read from there.  The epilogue computes the moments of the new values
+// (chunk_moments).  Returns false when the staging copies failed.
+template <typename S, typename C, bool BULK>
+__device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, unsigned char* smem_raw, int lane, int wy) {
     C* stab = reinterpret_cast<C*>(smem_raw);
     void* tws = smem_raw + upd_table_bytes(I.ntab, sizeof(C));
-    S* fo = reinterpret_cast<S*>(static_cast<unsigned char*>(tws) + TW_BYTES);
-    double* ex = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(fo) + (size_t)I.ukc * TILE * sizeof(S));
+    S* Sw = reinterpret_cast<S*>(smem_raw + upd_stage_offset(I.ntab, sizeof(C)));
+    double* ex = reinterpret_cast<double*>(Sw);                 // after the rows are consumed
+    S* fo = reinterpret_cast<S*>(smem_raw + upd_fo_offset(I.ntab, I.ukc, sizeof(C), sizeof(S)));
     const int i = i0 + lane;
     const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, ntab = I.ntab;
     const bool valid = i < N;
@@ -1467,7 +1602,8 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const C* gLc = Tabs<C>::gL(I);
     const C* gRc = Tabs<C>::gR(I);
     const C* Kyc = Tabs<C>::Ky(I);
-    __syncthreads();                      // the previous item's readers of the table are done
+    __syncthreads();                      // the previous item's readers of shared memory are done
+    if (!stage_rows<S, BULK>(I, i0, k0, k1 - k0, stage, Sw, fo, lane, wy)) return false;
     // rows in batches: all loads of a batch are issued before its shared-memory stores
     constexpr int TB = 16;
     for (int r0 = wy; r0 < ntab; r0 += UPD_WARPS * TB) {
@@ -1487,7 +1623,6 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     __syncthreads();
     const S* src = static_cast<const S*>(I.f[stage - 1]);
     S* dst = static_cast<S*>(I.f[stage % 3]);
-    const S* F = static_cast<const S*>(I.f[0]);
     const C ca = stage == 1 ? (C)0 : (stage == 2 ? (C)0.75 : (C)(1.0 / 3.0));
     const C cb = stage == 1 ? (C)1 : (stage == 2 ? (C)0.25 : (C)(2.0 / 3.0));
     const C dt = (C)I.dt;
@@ -1499,15 +1634,23 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const int Tz = I.form == FORM_UNREDUCED ? I.Qz : 2;
     const C ay = (C)I.accel_y;
     const C sixth = (C)(1.0 / 6.0);
-    // node values i-3 .. i+3 of velocity k with ghost cells (Sec. III B): incoming populations
-    // take the wall Maxwellian n_w g; outgoing ones the quadratic extrapolation of nodes 0..2
-    auto gather = [&](int k, bool pos, C* v) {
-        const S* row = src + (size_t)k * ld;
+    // every stencil node of the tile inside the domain: no ghost cells (block-uniform)
+    const bool interior = i0 >= 3 && i0 + TILE + 3 <= N;
+    // (kx, t) of the warp's velocities k = k0 + wy + UPD_WARPS m, stepped without divisions
+    int kx = (k0 + wy) / Tc, t = (k0 + wy) - kx * Tc;
+    for (int k = k0 + wy; k < k1; k += UPD_WARPS) {
+        const bool pos = kx < Q;
+        const C p = pxc[kx];
+        // node values i-3 .. i+3 (staged node j at row index j - i0 + 4) with the ghost cells of
+        // the diffuse walls (Sec. III B): incoming populations take the wall Maxwellian n_w g,
+        // outgoing ones the quadratic extrapolation of the three nodes next to the wall
+        const S* row = Sw + (k - k0) * SW + 4 - i0;
+        C v[7];
 #pragma unroll
         for (int jj = 0; jj < 7; ++jj) {
             const int j = i - 3 + jj;
             C val;
-            if (j >= 0 && j < N) {
+            if (interior || (j >= 0 && j < N)) {
                 val = (C)row[j];
             } else if (j < 0) {
                 if (pos) {
@@ -1526,34 +1669,6 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
             }
             v[jj] = val;
         }
-    };
-    // the loads of the warp's next velocity are issued before the current one is computed
-    // (kx, t) of the warp's velocities k = k0 + wy + UPD_WARPS m, stepped without divisions
-    int kx = (k0 + wy) / Tc, t = (k0 + wy) - kx * Tc;
-    int kxn = kx, tn = t + UPD_WARPS;
-    while (tn >= Tc) { tn -= Tc; ++kxn; }
-    C vn[7], Fn = 0;
-    if (k0 + wy < k1) {
-        gather(k0 + wy, kx < Q, vn);
-        if (stage != 1 && valid) Fn = (C)F[(size_t)(k0 + wy) * ld + i];
-    }
-    auto advance = [&]() {
-        kx = kxn;
-        t = tn;
-        tn += UPD_WARPS;
-        while (tn >= Tc) { tn -= Tc; ++kxn; }
-    };
-    for (int k = k0 + wy; k < k1; k += UPD_WARPS, advance()) {
-        const bool pos = kx < Q;
-        const C p = pxc[kx];
-        C v[7];
-#pragma unroll
-        for (int jj = 0; jj < 7; ++jj) v[jj] = vn[jj];
-        const C Fk = Fn;
-        if (k + UPD_WARPS < k1) {
-            gather(k + UPD_WARPS, kxn < Q, vn);
-            if (stage != 1 && valid) Fn = (C)F[(size_t)(k + UPD_WARPS) * ld + i];
-        }
         // right face (i + 1/2)
         C fr;
         if (i + 1 == N) fr = pos ? (11 * v[3] - 7 * v[2] + 2 * v[1]) * sixth : nwR * gRc[k];
@@ -1563,42 +1678,50 @@ __device__ void update_item(const Inst& I, int i0, int k0, int k1, int stage, un
             if (i == 0) fl = pos ? nwL * gLc[k] : (11 * v[3] - 7 * v[4] + 2 * v[5]) * sixth;
             else fl = pos ? weno_face(v[0], v[1], v[2], v[3], v[4]) : weno_face(v[5], v[4], v[3], v[2], v[1]);
         }
-        if (!valid) {
-            fo[(k - k0) * TILE + lane] = (S)0;
-            continue;
-        }
-        C L = -xpi * p * (fr - fl);
-        if (force) {
-            const int ky = t / Tz, kz = t - ky * Tz;
-            const C* Kr = Kyc + ky * I.Qy;
-            C d = 0;
-            for (int kp = 0; kp < I.Qy; ++kp) d += Kr[kp] * (C)src[(size_t)(kx * Tc + kp * Tz + kz) * ld + i];
-            L -= ay * d;
-        }
-        C tgt = 0;
+        S* fk = fo + (k - k0) * TILE + lane;
+        if (valid) {
+            C L = -xpi * p * (fr - fl);
+            if (force) {
+                const int ky = t / Tz, kz = t - ky * Tz;
+                const C* Kr = Kyc + ky * I.Qy;
+                C d = 0;
+                for (int kp = 0; kp < I.Qy; ++kp) d += Kr[kp] * (C)src[(size_t)(kx * Tc + kp * Tz + kz) * ld + i];
+                L -= ay * d;
+            }
+            C tgt = 0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) tgt += stab[(a * 2 * Q + kx) * TILE + lane] * stab[(8 * Q + a * Tc + t) * TILE + lane];
-        const C fi = v[3];
-        L += (tgt - fi) * invtau;
-        C out;
-        if constexpr (sizeof(C) == 4) {
-            // FP32: the same combination written as an increment of F, F + cb ((f - F) + dt L)
-            // (stage 1: f + dt L).  In the printed form ca F + cb (f + dt L) the rounded
-            // weights (float) 1/3 + (float) 2/3 = 1 + 3e-8 scale a steady f up by half an ulp
-            // every step, a mass drift of ~1e-3 over a solve; the increment form has no such
-            // bias.  The sum is stored with stochastic rounding (sr_add).
-            const C base = stage == 1 ? fi : Fk;
-            const C inc = stage == 1 ? dt * L : cb * ((fi - Fk) + dt * L);
-            out = sr_add(base, inc, fmix32(((uint32_t)k * (uint32_t)ld + (uint32_t)i) ^ seed));
+            for (int a = 0; a < 4; ++a) tgt += stab[(a * 2 * Q + kx) * TILE + lane] * stab[(8 * Q + a * Tc + t) * TILE + lane];
+            const C fi = v[3];
+            const C Fk = stage == 1 ? (C)0 : (C)*fk;
+            L += (tgt - fi) * invtau;
+            C out;
+            if constexpr (sizeof(C) == 4) {
+                // FP32: the same combination written as an increment of F, F + cb ((f - F) + dt L)
+                // (stage 1: f + dt L).  In the printed form ca F + cb (f + dt L) the rounded
+                // weights (float) 1/3 + (float) 2/3 = 1 + 3e-8 scale a steady f up by half an ulp
+                // every step, a mass drift of ~1e-3 over a solve; the increment form has no such
+                // bias.  The sum is stored with stochastic rounding (sr_add).
+                const C base = stage == 1 ? fi : Fk;
+                const C inc = stage == 1 ? dt * L : cb * ((fi - Fk) + dt * L);
+                out = sr_add(base, inc, fmix32(((uint32_t)k * (uint32_t)ld + (uint32_t)i) ^ seed));
+            } else {
+                out = cb * (fi + dt * L);
+                if (stage != 1) out += ca * Fk;
+            }
+            dst[(size_t)k * ld + i] = (S)out;
+            *fk = (S)out;
         } else {
-            out = cb * (fi + dt * L);
-            if (stage != 1) out += ca * Fk;
+            *fk = (S)0;
         }
-        dst[(size_t)k * ld + i] = (S)out;
-        fo[(k - k0) * TILE + lane] = (S)out;
+        t += UPD_WARPS;
+        while (t >= Tc) {
+            t -= Tc;
+            ++kx;
+        }
     }
-    __syncthreads();
+    __syncthreads();                      // every warp is done with the staged rows (ex aliases them)
     chunk_moments<S>(I, i0, k0, k1, k0 / I.ukc, fo, ex, tws, lane, wy);
+    return true;
 }
 
 template <typename S, typename C>
@@ -1608,10 +1731,8 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE) return;
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
-    update_item<S, C>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y);
-    if (I.mgroups > 1)
-        chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_table_bytes(I.ntab, sizeof(C)) + TW_BYTES +
-                                                              (size_t)I.ukc * TILE * sizeof(S)) + UPD_WARPS * MOM_SUMS * TILE);
+    if (!update_item<S, C, true>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y)) return;
+    if (I.mgroups > 1) chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_stage_offset(I.ntab, sizeof(C))) + UPD_WARPS * MOM_SUMS * TILE);
 }
 
 // Moments of buffer `buf` from scratch (creation, new profiles, a loaded state): one block per
@@ -1676,7 +1797,7 @@ __device__ void res_step(Inst& I, int idx, double tol, double* resid_all, int ra
         cl.sync();
         for (int it = rank; it < tiles * nch; it += CS) {
             const int tl = it / nch, c = it - tl * nch, k0 = c * KC;
-            update_item<S, S>(I, tl * TILE, k0, min(K, k0 + KC), stage, sm, lane, wy);
+            update_item<S, S, false>(I, tl * TILE, k0, min(K, k0 + KC), stage, sm, lane, wy);
         }
         cl.sync();
         if (nch > 1) res_final<S>(I, rank, CS, sm, cl);

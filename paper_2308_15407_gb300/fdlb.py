@@ -23,7 +23,7 @@ XQ_HALF, XQ_FULL = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32_STORAGE, "fp32+fp64": FP32_THEN_FP64}
 SCHED_AUTO, SCHED_TILED, SCHED_RESIDENT = 0, 1, 2
 SCHEDULES = {"auto": SCHED_AUTO, "tiled": SCHED_TILED, "resident": SCHED_RESIDENT}
-ACTIVE, CONVERGED, FAILED_NONFINITE, FAILED_UNPHYSICAL, STAGNATED = 0, 1, 2, 3, 4
+ACTIVE, CONVERGED, FAILED_NONFINITE, FAILED_UNPHYSICAL, STAGNATED, FAILED_COPY = 0, 1, 2, 3, 4, 5
 MOMENT_ROWS = ("n", "ux", "uy", "T", "qx", "qy", "Pxx", "Pxy")
 
 
