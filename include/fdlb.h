@@ -237,22 +237,34 @@ int fdlb_set_state(fdlb_ctx* ctx, int32_t inst, const void* host, size_t bytes);
  *             inside a step; on the GB300 the tiled schedule still measured faster on every
  *             workload tried (one instance: 113 against 244 us per RK3 step), because it
  *             spreads an instance's latency-bound items over more SMs than a cluster has.
+ *   MIXED:    the instances whose three RK buffers fit in one block's shared memory together
+ *             with the items' scratch (fdlb_get_schedule_mix; not FDLB_FP32_THEN_FP64) are
+ *             stepped by one CTA each that keeps f in shared memory across all stages and steps
+ *             of the call (f crosses HBM once at the start and once at the end of the call);
+ *             the other instances take the tiled steps at the same time, on a second stream
+ *             that the call forks from and joins back into the context's stream.
  *   AUTO:     (default) the first fdlb_step call with at least FDLB_AUTOTUNE_STEPS steps
- *             times both (its own steps, half each) and keeps the faster; shorter calls use
- *             TILED until then.
+ *             times every available schedule (its own steps, an equal share each) and keeps the
+ *             fastest; shorter calls use TILED until then.
  * fdlb_profile's per-kernel timing always uses the tiled schedule. */
 #define FDLB_SCHED_AUTO      0
 #define FDLB_SCHED_TILED     1
 #define FDLB_SCHED_RESIDENT  2
+#define FDLB_SCHED_MIXED     3
 #define FDLB_AUTOTUNE_STEPS  96
 
 /* Request a schedule (FDLB_EINVAL for RESIDENT when the device cannot launch the cluster
- * kernel for this batch). */
+ * kernel for this batch, and for MIXED when no instance fits in shared memory). */
 int fdlb_set_schedule(fdlb_ctx* ctx, int32_t schedule);
 
 /* Schedule in use (FDLB_SCHED_AUTO while not chosen yet) and the CTAs per cluster of the
  * resident schedule (0 when it is unavailable).  Either pointer may be NULL. */
 int fdlb_get_schedule(const fdlb_ctx* ctx, int32_t* schedule, int32_t* cluster_ctas);
+
+/* Which instances FDLB_SCHED_MIXED keeps in shared memory (chosen by size at creation):
+ * smem_resident[count] (may be NULL) receives 1 for those, 0 for the others; *n (may be NULL)
+ * their number (0: FDLB_SCHED_MIXED is unavailable for this batch). */
+int fdlb_get_schedule_mix(const fdlb_ctx* ctx, int32_t* smem_resident, int32_t* n);
 
 /* Optional per-kernel timing with CUDA events recorded on the context's stream around every
  * launch (off by default).  fdlb_profile(ctx, 1) clears the records and starts recording,

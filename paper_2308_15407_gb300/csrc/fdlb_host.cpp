@@ -53,6 +53,16 @@ struct fdlb_ctx {
     int sched_req = FDLB_SCHED_AUTO, sched = 0;
     int cs = 0;                       // CTAs per cluster of the resident schedule (0: unavailable)
     size_t res_smem = 0;
+    // shared-memory-resident schedule (part of FDLB_SCHED_MIXED): the instances whose three RK
+    // buffers fit in one block's shared memory, stepped by k_smemres on a second stream
+    int* d_smem_list = nullptr;       // count ints (the first n_smem used)
+    std::vector<int> smem_idx;
+    int n_smem = 0, smem_qmax = 1;
+    size_t smem_scratch = 0, smem_dyn = 0;
+    bool smem_flags = false;          // smem_res set on the device for the listed instances
+    std::string smem_note;            // how the set was chosen (for the error message)
+    cudaStream_t stream2 = nullptr;   // created on first use of FDLB_SCHED_MIXED
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     // CUDA graph of GRAPH_STEPS steps for one freeze tolerance (replayed by fdlb_step)
     cudaGraphExec_t graph = nullptr;
@@ -66,10 +76,14 @@ struct fdlb_ctx {
         for (auto& v : ev)
             for (auto e : v) cudaEventDestroy(e);
         if (graph) cudaGraphExecDestroy(graph);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (stream2) cudaStreamDestroy(stream2);
     }
 };
 
 static void choose_cluster(fdlb_ctx* c);
+static void choose_smem_resident(fdlb_ctx* c);
 
 // Record a start/stop event pair around one launch of class `kind` when profiling is on.
 static cudaError_t prof_mark(fdlb_ctx* c, int kind) {
@@ -476,7 +490,7 @@ Layout layout_of(const fdlb_params& p, int ukc) {
 size_t global_bytes(int count, int n_upd, int n_nod) {
     return al256(sizeof(Inst) * count) + al256(sizeof(Work) * n_upd) + al256(sizeof(Work) * n_nod) +
            al256(sizeof(int) * count) + al256(sizeof(long long) * count) + al256(sizeof(double) * count) +
-           al256(sizeof(int) * count);
+           al256(sizeof(int) * count) + al256(sizeof(int) * count);
 }
 
 void count_work(const std::vector<fdlb_params>& p, int& n_upd, int& n_nod) {
@@ -541,6 +555,7 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
     c->d_steps_all = reinterpret_cast<long long*>(take(sizeof(long long) * count));
     c->d_resid_all = reinterpret_cast<double*>(take(sizeof(double) * count));
     c->d_list = reinterpret_cast<int*>(take(sizeof(int) * count));
+    c->d_smem_list = reinterpret_cast<int*>(take(sizeof(int) * count));
 
     std::vector<Work> wu, wn;
     std::vector<std::pair<int*, size_t>> counters;
@@ -839,6 +854,12 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         return (long)c->inst[a].N * c->inst[a].K > (long)c->inst[b].N * c->inst[b].K;
     });
     rc = cuda_check(c, cudaMemcpyAsync(c->d_list, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s), "upload list");
+    if (!rc) {
+        choose_smem_resident(c);
+        if (c->n_smem > 0)
+            rc = cuda_check(c, cudaMemcpyAsync(c->d_smem_list, c->smem_idx.data(), sizeof(int) * c->n_smem, cudaMemcpyHostToDevice, s),
+                            "upload list");
+    }
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "upload list");
     if (rc) { int e = rc; g_err = c->err; delete c; return e; }
     rc = cuda_check(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s), "upload descriptors");
@@ -922,6 +943,67 @@ static void choose_cluster(fdlb_ctx* c) {
     }
 }
 
+// Instances for the shared-memory-resident kernel: not two-phase, and the item scratch plus the
+// three RK buffers fit in one block's dynamic shared memory.  The kernel is launched with one
+// size for all of them (the largest scratch and buffers of the set), so the instances with the
+// largest need leave the set until that size fits.  Largest first in the launch order.
+static void choose_smem_resident(fdlb_ctx* c) {
+    c->n_smem = 0;
+    c->smem_idx.clear();
+    struct Cand { int idx, Lx; size_t upd, fb, need; };
+    std::vector<Cand> cand;
+    size_t limit = 0;
+    int qall = 1;
+    for (auto& I : c->inst) qall = std::max(qall, I.Lx);
+    if (smemres_dynamic_limit(qall, &limit) != cudaSuccess) { cudaGetLastError(); return; }
+    for (int i = 0; i < c->count; ++i) {
+        const Inst& I = c->inst[i];
+        if (I.two_phase) continue;
+        const size_t sz = I.precision == FDLB_FP32_STORAGE ? 4 : 8;
+        const size_t upd = update_smem_bytes(I.ntab, I.ukc, sz, sz);
+        const size_t fb = smemres_buffer_bytes(I.K, I.ld, sz);
+        const size_t need = smemres_scratch_bytes(I.Lx, upd) + 3 * fb;
+        if (need <= limit) cand.push_back({i, I.Lx, upd, fb, need});
+    }
+    std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.need > b.need; });
+    size_t first = 0;
+    int qm = 1;
+    size_t scratch = 0, dyn = 0;
+    cudaError_t attr = cudaSuccess;
+    while (first < cand.size()) {
+        size_t um = 0, fm = 0;
+        qm = 1;
+        for (size_t j = first; j < cand.size(); ++j) { qm = std::max(qm, cand[j].Lx); um = std::max(um, cand[j].upd); fm = std::max(fm, cand[j].fb); }
+        scratch = smemres_scratch_bytes(qm, um);
+        dyn = scratch + 3 * fm;
+        if (dyn <= limit) {
+            attr = prepare_smemres(qm, dyn);
+            if (attr == cudaSuccess) break;
+            cudaGetLastError();
+        }
+        ++first;
+    }
+    size_t least = 0;
+    for (auto& cd : cand) least = least ? std::min(least, cd.need) : cd.need;
+    c->smem_note = "dynamic shared memory per block " + std::to_string(limit) + " B; " + std::to_string(cand.size()) +
+                   " candidates" + (cand.empty() ? "" : ", smallest need " + std::to_string(least) + " B") +
+                   (attr != cudaSuccess ? std::string(", attribute: ") + cudaGetErrorString(attr) : std::string());
+    if (first >= cand.size()) return;
+    for (size_t j = first; j < cand.size(); ++j) c->smem_idx.push_back(cand[j].idx);
+    c->n_smem = (int)c->smem_idx.size();
+    c->smem_qmax = qm;
+    c->smem_scratch = scratch;
+    c->smem_dyn = dyn;
+}
+
+// smem_res of the listed instances on the device (the tiled kernels skip flagged instances).
+static int set_smem_flags(fdlb_ctx* c, bool on) {
+    if (c->smem_flags == on || c->n_smem == 0) return FDLB_OK;
+    int rc = cuda_check(c, launch_set_smem_flags(c->d_inst, c->d_smem_list, c->n_smem, on ? 1 : 0, c->stream), "schedule flags");
+    if (!rc) c->smem_flags = on;
+    return rc;
+}
+
 // Capture GRAPH_STEPS steps into an executable graph (kernels only; no host synchronisation
 // inside).  The legacy default stream cannot be captured: then steps are launched directly.
 static bool ensure_graph(fdlb_ctx* c, double tol) {
@@ -981,39 +1063,79 @@ static int step_resident(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
     return FDLB_OK;
 }
 
-// Times TUNE steps of each schedule (after 16 warm-up steps of each) and keeps the faster.
+// Mixed schedule: the shared-memory-resident instances advance in one k_smemres launch on the
+// second stream while the others take the tiled steps on the context's stream; the call's work
+// is joined back into the context's stream.
+static int step_mixed(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
+    int rc = FDLB_OK;
+    if (!c->stream2) {
+        rc = cuda_check(c, cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking), "second stream");
+        if (!rc) rc = cuda_check(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "stream events");
+        if (!rc) rc = cuda_check(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "stream events");
+        if (rc) return rc;
+    }
+    rc = set_smem_flags(c, true);
+    if (!rc) rc = cuda_check(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
+    if (!rc) rc = cuda_check(c, cudaStreamWaitEvent(c->stream2, c->ev_fork, 0), "fork");
+    int64_t left = nsteps;
+    while (!rc && left > 0) {
+        const int n = (int)std::min<int64_t>(left, 1 << 20);
+        rc = cuda_check(c, launch_smemres(c->d_inst, c->d_smem_list, c->n_smem, c->smem_qmax, c->smem_scratch, c->smem_dyn, n,
+                                          freeze_tol, c->d_resid_all, c->stream2), "shared-memory-resident launch");
+        left -= n;
+    }
+    if (!rc && c->n_smem < c->count) rc = step_tiled(c, nsteps, freeze_tol);
+    if (!rc) rc = cuda_check(c, cudaEventRecord(c->ev_join, c->stream2), "join");
+    if (!rc) rc = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
+    return rc;
+}
+
+static int step_schedule(fdlb_ctx* c, int sched, int64_t nsteps, double freeze_tol) {
+    if (sched == FDLB_SCHED_MIXED) return step_mixed(c, nsteps, freeze_tol);
+    int rc = set_smem_flags(c, false);
+    if (rc) return rc;
+    return sched == FDLB_SCHED_RESIDENT ? step_resident(c, nsteps, freeze_tol) : step_tiled(c, nsteps, freeze_tol);
+}
+
+// Times TUNE steps of each available schedule (after WARM warm-up steps of each) and keeps the
+// fastest: tiled, cluster-resident, and mixed (shared-memory-resident for the instances that fit).
 static int autotune(fdlb_ctx* c, double freeze_tol) {
-    const int WARM = 16, TUNE = (FDLB_AUTOTUNE_STEPS - 2 * WARM) / 2;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<int> cands = {FDLB_SCHED_TILED};
+    if (c->cs > 0) cands.push_back(FDLB_SCHED_RESIDENT);
+    if (c->n_smem > 0) cands.push_back(FDLB_SCHED_MIXED);
+    const int WARM = 16, TUNE = (FDLB_AUTOTUNE_STEPS - (int)cands.size() * WARM) / (int)cands.size();
+    std::vector<cudaEvent_t> ev(2 * cands.size(), nullptr);
     int rc = FDLB_OK;
     for (auto& e : ev)
         if (!rc) rc = cuda_check(c, cudaEventCreate(&e), "autotune events");
-    if (!rc) rc = step_tiled(c, WARM, freeze_tol);
-    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[0], c->stream), "autotune events");
-    if (!rc) rc = step_tiled(c, TUNE, freeze_tol);
-    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[1], c->stream), "autotune events");
-    if (!rc) rc = step_resident(c, WARM, freeze_tol);
-    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[2], c->stream), "autotune events");
-    if (!rc) rc = step_resident(c, TUNE, freeze_tol);
-    if (!rc) rc = cuda_check(c, cudaEventRecord(ev[3], c->stream), "autotune events");
-    float t_tiled = 0.0f, t_res = 0.0f;
-    if (!rc) rc = cuda_check(c, cudaEventSynchronize(ev[3]), "autotune synchronize");
-    if (!rc) rc = cuda_check(c, cudaEventElapsedTime(&t_tiled, ev[0], ev[1]), "autotune timing");
-    if (!rc) rc = cuda_check(c, cudaEventElapsedTime(&t_res, ev[2], ev[3]), "autotune timing");
+    for (size_t j = 0; j < cands.size() && !rc; ++j) {
+        rc = step_schedule(c, cands[j], WARM, freeze_tol);
+        if (!rc) rc = cuda_check(c, cudaEventRecord(ev[2 * j], c->stream), "autotune events");
+        if (!rc) rc = step_schedule(c, cands[j], TUNE, freeze_tol);
+        if (!rc) rc = cuda_check(c, cudaEventRecord(ev[2 * j + 1], c->stream), "autotune events");
+    }
+    if (!rc) rc = cuda_check(c, cudaEventSynchronize(ev.back()), "autotune synchronize");
+    float best = 0.0f;
+    int pick = FDLB_SCHED_TILED;
+    for (size_t j = 0; j < cands.size() && !rc; ++j) {
+        float t = 0.0f;
+        rc = cuda_check(c, cudaEventElapsedTime(&t, ev[2 * j], ev[2 * j + 1]), "autotune timing");
+        if (!rc && (j == 0 || t < best)) { best = t; pick = cands[j]; }
+    }
     for (auto e : ev)
         if (e) cudaEventDestroy(e);
-    if (!rc) c->sched = t_res < t_tiled ? FDLB_SCHED_RESIDENT : FDLB_SCHED_TILED;
+    if (!rc) c->sched = pick;
     return rc;
 }
 
 extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
     if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_step: null context");
     if (nsteps < 0 || !(freeze_tol >= 0)) return fail(c, FDLB_EINVAL, "fdlb_step: nsteps >= 0 and freeze_tol >= 0 required");
-    if (c->prof) return step_tiled(c, nsteps, freeze_tol);
+    if (c->prof) return step_schedule(c, FDLB_SCHED_TILED, nsteps, freeze_tol);
     if (c->sched == 0) {
         if (c->sched_req != FDLB_SCHED_AUTO) {
             c->sched = c->sched_req;
-        } else if (c->cs == 0) {
+        } else if (c->cs == 0 && c->n_smem == 0) {
             c->sched = FDLB_SCHED_TILED;
         } else if (nsteps >= FDLB_AUTOTUNE_STEPS) {
             int rc = autotune(c, freeze_tol);
@@ -1021,16 +1143,19 @@ extern "C" int fdlb_step(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
             nsteps -= FDLB_AUTOTUNE_STEPS;
         }
     }
-    if (c->sched == FDLB_SCHED_RESIDENT) return step_resident(c, nsteps, freeze_tol);
-    return step_tiled(c, nsteps, freeze_tol);
+    return step_schedule(c, c->sched == 0 ? FDLB_SCHED_TILED : c->sched, nsteps, freeze_tol);
 }
 
 extern "C" int fdlb_set_schedule(fdlb_ctx* c, int32_t schedule) {
     if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_set_schedule: null context");
-    if (schedule != FDLB_SCHED_AUTO && schedule != FDLB_SCHED_TILED && schedule != FDLB_SCHED_RESIDENT)
+    if (schedule != FDLB_SCHED_AUTO && schedule != FDLB_SCHED_TILED && schedule != FDLB_SCHED_RESIDENT &&
+        schedule != FDLB_SCHED_MIXED)
         return fail(c, FDLB_EINVAL, "fdlb_set_schedule: unknown schedule");
     if (schedule == FDLB_SCHED_RESIDENT && c->cs == 0)
         return fail(c, FDLB_EINVAL, "fdlb_set_schedule: the resident cluster kernel cannot be launched for this batch");
+    if (schedule == FDLB_SCHED_MIXED && c->n_smem == 0)
+        return fail(c, FDLB_EINVAL, "fdlb_set_schedule: no instance of this batch fits in one block's shared memory (" +
+                                        c->smem_note + ")");
     c->sched_req = schedule;
     c->sched = schedule == FDLB_SCHED_AUTO ? 0 : schedule;
     return FDLB_OK;
@@ -1040,6 +1165,16 @@ extern "C" int fdlb_get_schedule(const fdlb_ctx* c, int32_t* schedule, int32_t* 
     if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_get_schedule: null context");
     if (schedule) *schedule = c->sched;
     if (cluster_ctas) *cluster_ctas = c->cs;
+    return FDLB_OK;
+}
+
+extern "C" int fdlb_get_schedule_mix(const fdlb_ctx* c, int32_t* smem_resident, int32_t* n) {
+    if (!c) return fail(nullptr, FDLB_EINVAL, "fdlb_get_schedule_mix: null context");
+    if (n) *n = c->n_smem;
+    if (smem_resident) {
+        for (int i = 0; i < c->count; ++i) smem_resident[i] = 0;
+        for (int i : c->smem_idx) smem_resident[i] = 1;
+    }
     return FDLB_OK;
 }
 

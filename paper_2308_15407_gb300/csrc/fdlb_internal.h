@@ -52,6 +52,7 @@ struct Inst {
     uint32_t sr_key;           // hash of the parameters: seeds the stochastic rounding of FP32 storage
     int ukc;                   // velocities per update block (chunk) of a tile
     int mgroups;               // update chunks per tile (> 1: partial moment sums in msum)
+    int smem_res;              // 1: stepped by the shared-memory-resident kernel (the tiled kernels skip it)
     double kn, eta0, chi0, mu0c, dt, ds, accel_y;
     double T_L, T_R, U_L, U_R, T_init;
     double x_h0;               // h_0 of the x axis' orthonormal family

@@ -1037,7 +1037,7 @@ __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restri
     extern __shared__ __align__(16) double nsm[];
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
-    if (*I.status != FDLB_ACTIVE) return;
+    if (*I.status != FDLB_ACTIVE || I.smem_res) return;
     nodal_item<QB>(I, w.i0, w.k0, nsm, I.precision == FDLB_FP32_STORAGE);
 }
 
@@ -1191,7 +1191,7 @@ __global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double t
         }
         return;
     }
-    if (*I.status != FDLB_ACTIVE) return;
+    if (*I.status != FDLB_ACTIVE || I.smem_res) return;
     resid_item(I, blockIdx.x, tol, resid_all);
 }
 
@@ -1729,7 +1729,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
-    if (*I.status != FDLB_ACTIVE) return;
+    if (*I.status != FDLB_ACTIVE || I.smem_res) return;
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     if (!update_item<S, C, true>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y)) return;
     if (I.mgroups > 1) chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_stage_offset(I.ntab, sizeof(C))) + UPD_WARPS * MOM_SUMS * TILE);
@@ -1833,6 +1833,71 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(Inst* insts, const 
 }
 
 // ---------------------------------------------------------------------------
+// shared-memory-resident schedule: one CTA per instance keeps f in shared memory
+// ---------------------------------------------------------------------------
+// The CTA runs whole steps of its instance with the items of the tiled kernels (identical
+// arithmetic) on a block-local copy of the instance record whose three RK buffers point into
+// dynamic shared memory: f crosses HBM only when the launch starts and ends.  Tables, node rows
+// and partial sums stay in global memory (L2).  Stages are separated by block barriers.
+__host__ __device__ inline size_t smemres_f_bytes(int K, int ld, size_t s) { return ((size_t)K * ld * s + 15) / 16 * 16; }
+
+template <int QB, typename S>
+__device__ void smem_step(Inst& I, int idx, double tol, double* resid_all, unsigned char* sm) {
+    const int tiles = (I.N + TILE - 1) / TILE, K = I.K, KC = I.ukc, nch = I.mgroups;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    for (int stage = 1; stage <= 3; ++stage) {
+        for (int it = 0; it < 3 * tiles; ++it)
+            nodal_item<QB>(I, (it / 3) * TILE, it % 3, reinterpret_cast<double*>(sm), sizeof(S) == 4);
+        __syncthreads();
+        for (int it = 0; it < tiles * nch; ++it) {
+            const int tl = it / nch, c = it - tl * nch, k0 = c * KC;
+            update_item<S, S, false>(I, tl * TILE, k0, min(K, k0 + KC), stage, sm, lane, wy);
+        }
+        __syncthreads();
+        if (nch > 1) {
+            // moments of chunked tiles from their partials, by 128-thread halves
+            const int half = threadIdx.x >> 7;
+            double* ss = reinterpret_cast<double*>(sm) + half * MOM_SUMS * TILE;
+            for (int tl = half; tl < tiles; tl += 2) moments_final_tile<S>(I, tl * TILE, ss, threadIdx.x & 127, 4, 1 + half);
+            __syncthreads();
+        }
+    }
+    resid_item(I, idx, tol, resid_all);
+    __syncthreads();
+}
+
+// Block b advances instance list[b] by up to nsteps steps; dynamic shared memory = scratch
+// bytes for the items, then the three RK buffers.
+template <int QB>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_smemres(Inst* insts, const int* list, int nsteps, double tol, double* resid_all,
+                                                            size_t scratch) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    __shared__ Inst Is;
+    const int idx = list[blockIdx.x];
+    Inst& Ig = insts[idx];
+    if (*(volatile int*)Ig.status != FDLB_ACTIVE) return;
+    if (threadIdx.x == 0) Is = Ig;
+    __syncthreads();
+    const bool fp32 = Is.precision == FDLB_FP32_STORAGE;
+    const size_t bytes = (size_t)Is.K * Is.ld * (fp32 ? 4 : 8);          // a multiple of 128
+    const size_t fb = smemres_f_bytes(Is.K, Is.ld, fp32 ? 4 : 8);
+    unsigned char* fs = rsm + scratch;
+    uint4* gF = static_cast<uint4*>(Ig.f[0]);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < 3; ++b) Is.f[b] = fs + b * fb;
+    uint4* sF = reinterpret_cast<uint4*>(fs);
+    for (size_t e = threadIdx.x; e < bytes / 16; e += blockDim.x) sF[e] = gF[e];
+    __syncthreads();
+    for (int step = 0; step < nsteps; ++step) {
+        if (*(volatile int*)Is.status != FDLB_ACTIVE) break;              // written by this block
+        if (fp32) smem_step<QB, float>(Is, idx, tol, resid_all, rsm);
+        else smem_step<QB, double>(Is, idx, tol, resid_all, rsm);
+    }
+    for (size_t e = threadIdx.x; e < bytes / 16; e += blockDim.x) gF[e] = sF[e];
+}
+
+// ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
 // Kernel attributes (dynamic shared memory above 48 KB, non-portable cluster sizes) and the
@@ -1846,6 +1911,7 @@ struct DevAttr {
     int nodal = 0;
     size_t mom64 = 0, mom32 = 0, upd64 = 0, upd32 = 0;
     size_t res[2] = {0, 0};
+    size_t smemres[2] = {0, 0};
     bool nonport[2] = {false, false};
 };
 std::mutex g_attr_mu;
@@ -2019,6 +2085,51 @@ cudaError_t launch_resident(Inst* d_inst, const int* d_list, int nclusters, int 
     cfg.numAttrs = 1;
     if (qmax <= 8) return cudaLaunchKernelEx(&cfg, k_resident<8>, d_inst, d_list, nsteps, freeze_tol, d_resid_all);
     return cudaLaunchKernelEx(&cfg, k_resident<QMAX>, d_inst, d_list, nsteps, freeze_tol, d_resid_all);
+}
+
+__global__ void k_set_smem_flags(Inst* insts, const int* list, int n, int on) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) insts[list[j]].smem_res = on;
+}
+
+cudaError_t launch_set_smem_flags(Inst* d_inst, const int* d_list, int n, int on, cudaStream_t s) {
+    if (n > 0) k_set_smem_flags<<<(n + 255) / 256, 256, 0, s>>>(d_inst, d_list, n, on);
+    return cudaGetLastError();
+}
+
+size_t smemres_scratch_bytes(int qmax, size_t upd_max) { return resident_smem_bytes(qmax, upd_max); }
+size_t smemres_buffer_bytes(int K, int ld, size_t s) { return smemres_f_bytes(K, ld, s); }
+
+// Dynamic shared memory available to k_smemres<QB>: the per-block maximum minus its static part.
+cudaError_t smemres_dynamic_limit(int qmax, size_t* limit) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = qmax <= 8 ? cudaFuncGetAttributes(&fa, k_smemres<8>) : cudaFuncGetAttributes(&fa, k_smemres<QMAX>);
+    if (e != cudaSuccess) return e;
+    *limit = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    return cudaSuccess;
+}
+
+cudaError_t prepare_smemres(int qmax, size_t dyn) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    DevAttr* A = nullptr;
+    cudaError_t e = dev_attr(&A);
+    if (e != cudaSuccess) return e;
+    const int slot = qmax <= 8 ? 0 : 1;
+    if (dyn > A->smemres[slot]) {
+        e = qmax <= 8 ? cudaFuncSetAttribute(k_smemres<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)
+                      : cudaFuncSetAttribute(k_smemres<QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e == cudaSuccess) A->smemres[slot] = dyn;
+    }
+    return e;
+}
+
+cudaError_t launch_smemres(Inst* d_inst, const int* d_list, int n, int qmax, size_t scratch, size_t dyn, int nsteps,
+                           double freeze_tol, double* d_resid_all, cudaStream_t s) {
+    if (qmax <= 8) k_smemres<8><<<n, RES_THREADS, dyn, s>>>(d_inst, d_list, nsteps, freeze_tol, d_resid_all, scratch);
+    else k_smemres<QMAX><<<n, RES_THREADS, dyn, s>>>(d_inst, d_list, nsteps, freeze_tol, d_resid_all, scratch);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,

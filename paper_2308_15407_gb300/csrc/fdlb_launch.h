@@ -46,6 +46,20 @@ cudaError_t resident_max_clusters(int qmax, size_t smem, int cs, int* n);
 cudaError_t launch_resident(Inst* d_inst, const int* d_list, int nclusters, int cs, int qmax, size_t smem, int nsteps,
                             double freeze_tol, double* d_resid_all, cudaStream_t s);
 
+// Shared-memory-resident schedule: one CTA per instance of d_list[0..n) keeps the instance's
+// three RK buffers in dynamic shared memory (after `scratch` bytes of item scratch) and runs up
+// to nsteps steps.  smemres_scratch_bytes: the item scratch for the batch's largest x order and
+// update-item shared memory; smemres_buffer_bytes: one RK buffer; smemres_dynamic_limit: the
+// dynamic shared memory a block of the kernel can have on this device.
+size_t smemres_scratch_bytes(int qmax, size_t upd_max);
+size_t smemres_buffer_bytes(int K, int ld, size_t s);
+cudaError_t smemres_dynamic_limit(int qmax, size_t* limit);
+cudaError_t prepare_smemres(int qmax, size_t dyn);
+// smem_res := on for the instances d_list[0..n) (the tiled kernels skip flagged instances).
+cudaError_t launch_set_smem_flags(Inst* d_inst, const int* d_list, int n, int on, cudaStream_t s);
+cudaError_t launch_smemres(Inst* d_inst, const int* d_list, int n, int qmax, size_t scratch, size_t dyn, int nsteps,
+                           double freeze_tol, double* d_resid_all, cudaStream_t s);
+
 // Shared-memory attributes of the kernels that need more than 48 KB (call outside any capture).
 cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax);
 

@@ -21,8 +21,8 @@ FP64, FP32_STORAGE, FP32_THEN_FP64 = 0, 1, 2
 CHI_SET, CHI_RET_FM = 0, 1
 XQ_HALF, XQ_FULL = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32_STORAGE, "fp32+fp64": FP32_THEN_FP64}
-SCHED_AUTO, SCHED_TILED, SCHED_RESIDENT = 0, 1, 2
-SCHEDULES = {"auto": SCHED_AUTO, "tiled": SCHED_TILED, "resident": SCHED_RESIDENT}
+SCHED_AUTO, SCHED_TILED, SCHED_RESIDENT, SCHED_MIXED = 0, 1, 2, 3
+SCHEDULES = {"auto": SCHED_AUTO, "tiled": SCHED_TILED, "resident": SCHED_RESIDENT, "mixed": SCHED_MIXED}
 ACTIVE, CONVERGED, FAILED_NONFINITE, FAILED_UNPHYSICAL, STAGNATED, FAILED_COPY = 0, 1, 2, 3, 4, 5
 MOMENT_ROWS = ("n", "ux", "uy", "T", "qx", "qy", "Pxx", "Pxy")
 
@@ -108,6 +108,7 @@ def load() -> C.CDLL:
         "fdlb_precision": (C.c_int, [vp, ip, lp]),
         "fdlb_set_schedule": (C.c_int, [vp, C.c_int32]),
         "fdlb_get_schedule": (C.c_int, [vp, ip, ip]),
+        "fdlb_get_schedule_mix": (C.c_int, [vp, ip, ip]),
         "fdlb_set_profiles": (C.c_int, [vp, C.c_int32, dp, dp, dp]),
         "fdlb_state_bytes": (C.c_size_t, [vp, C.c_int32]),
         "fdlb_get_state": (C.c_int, [vp, C.c_int32, vp, C.c_size_t]),
@@ -297,7 +298,9 @@ class Solver:
         return ch.value, g.value, t.value
 
     def set_schedule(self, schedule: str):
-        """'auto' (time both on the first long step call), 'tiled' or 'resident'."""
+        """'auto' (time every available schedule on the first long step call), 'tiled',
+        'resident' (one thread-block cluster per instance) or 'mixed' (instances that fit keep f
+        in shared memory, the others tiled)."""
         self._check(self.lib.fdlb_set_schedule(self.ctx, SCHEDULES[schedule]))
 
     def schedule(self):
@@ -305,6 +308,13 @@ class Solver:
         sc, cs = C.c_int32(), C.c_int32()
         self._check(self.lib.fdlb_get_schedule(self.ctx, C.byref(sc), C.byref(cs)))
         return {v: k for k, v in SCHEDULES.items()}[sc.value], cs.value
+
+    def schedule_mix(self) -> np.ndarray:
+        """Per instance 1 if FDLB_SCHED_MIXED keeps it in shared memory, else 0."""
+        out = np.zeros(self.count, dtype=np.int32)
+        n = C.c_int32()
+        self._check(self.lib.fdlb_get_schedule_mix(self.ctx, out.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)))
+        return out
 
     def precision_state(self):
         """(storage precision in use per instance, step of the FP32 -> FP64 switch or -1)."""

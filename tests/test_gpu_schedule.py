@@ -82,6 +82,6 @@ def test_autotune_picks_a_schedule_without_changing_results():
     sb.step(40)                       # shorter than the tuning window: tiled, no choice yet
     assert sb.schedule()[0] == "auto"
     sb.step(200)
-    assert sb.schedule()[0] in ("tiled", "resident")
+    assert sb.schedule()[0] in ("tiled", "resident", "mixed")
     sa.step(240)
     assert_same(sa, sb)
