@@ -125,27 +125,78 @@ __device__ __forceinline__ void put_bf16(unsigned char* base, int off, float v) 
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
 }
 
+// ------------------------------------------------------------------------------ packed weights
+// The BF16 core-matrix images of the weights that the forward and backward kernels use as
+// GEMM operands, written once per call from the FP32 master copy (k_mlp_pack) and copied into
+// each block's shared memory with bulk asynchronous copies.
+constexpr int PK_FWD = 106496;                 // W1t, W2t..W4t, W5t (the forward's first bytes)
+constexpr int PK_BWD = 102400;                 // W2n..W4n, W5n (the backward's first bytes)
+constexpr int PK_BYTES = PK_FWD + PK_BWD;
+
+__device__ __forceinline__ void bulk_copy(unsigned char* dst, const unsigned char* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(bar)) : "memory");
+}
+
+// bytes (a multiple of 4096, 16-byte aligned at both ends) into shared memory by the block's
+// threads, 4 KB per copy; false when the copies did not complete within the wait limit
+__device__ bool load_packed(unsigned char* dst, const unsigned char* src, int bytes, uint64_t* cbar) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(saddr(cbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(saddr(cbar)), "r"((uint32_t)bytes) : "memory");
+    }
+    __syncthreads();
+    for (int c = tid; c < bytes / 4096; c += blockDim.x) bulk_copy(dst + c * 4096, src + c * 4096, 4096, cbar);
+    return __syncthreads_and(wait_bar(cbar, 0) ? 1 : 0) != 0;
+}
+
+__global__ void k_mlp_pack(const float* __restrict__ prm, unsigned char* __restrict__ pk) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned char* fw = pk;
+    unsigned char* bw = pk + PK_FWD;
+    // forward operands B = W_l^T (rows: outputs, K = inputs); backward B = W_l (rows: inputs,
+    // K = outputs) for l >= 2; byte offsets as in the kernels' shared-memory layouts
+    if (e < OB1) {
+        const int k = e / NH, n = e % NH;
+        put_bf16(fw, cm(n, k, NIN), prm[e]);
+    } else {
+        for (int l = 2; l <= 4; ++l) {
+            const int q = e - woff(l);
+            if (q >= 0 && q < NH * NH) {
+                const int a = q / NH, b = q % NH;
+                put_bf16(fw + 4096 + (l - 2) * 32768, cm(b, a, NH), prm[e]);
+                put_bf16(bw + (l - 2) * 32768, cm(a, b, NH), prm[e]);
+            }
+        }
+        const int q = e - OW5;
+        if (q >= 0 && q < NH * NOUT) {
+            const int a = q / NOUT, b = q % NOUT;
+            put_bf16(fw + 4096 + 3 * 32768, cm(b, a, NH), prm[e]);
+            put_bf16(bw + 3 * 32768, cm(a, b, NOUT), prm[e]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------ forward
 // Shared bytes: W1t 4096 | W2t..W4t 3 x 32768 | W5t 4096 | A 32768 | bias 2112
 constexpr int F_W1 = 0, F_W2 = 4096, F_W3 = F_W2 + 32768, F_W4 = F_W3 + 32768, F_W5 = F_W4 + 32768;
 constexpr int F_A = F_W5 + 4096, F_BIAS = F_A + 32768, F_BYTES = F_BIAS + 4 * 4 * NH + 4 * NOUT;
 
-__global__ void __launch_bounds__(TILE) k_mlp_fwd(const float* __restrict__ prm, const float* __restrict__ X, int P,
-                                                  float* __restrict__ pred, float* __restrict__ Zs, int* err) {
+__global__ void __launch_bounds__(TILE) k_mlp_fwd(const float* __restrict__ prm, const unsigned char* __restrict__ pk,
+                                                  const float* __restrict__ X, int P, float* __restrict__ pred,
+                                                  float* __restrict__ Zs, int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, cbar;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x;
     const int p = blockIdx.x * TILE + tid;
     const bool valid = p < P;
     if (tid < 32) tmem_alloc(&tslot, NH);
-    // weights as B operands (N = outputs x K = inputs), biases
-    for (int e = tid; e < NIN * NH; e += TILE) { const int k = e / NH, n = e % NH; put_bf16(sm + F_W1, cm(n, k, NIN), prm[OW1 + e]); }
-    for (int l = 2; l <= 4; ++l) {
-        unsigned char* W = sm + (l == 2 ? F_W2 : l == 3 ? F_W3 : F_W4);
-        for (int e = tid; e < NH * NH; e += TILE) { const int k = e / NH, n = e % NH; put_bf16(W, cm(n, k, NH), prm[woff(l) + e]); }
-    }
-    for (int e = tid; e < NH * NOUT; e += TILE) { const int k = e / NOUT, n = e % NOUT; put_bf16(sm + F_W5, cm(n, k, NH), prm[OW5 + e]); }
+    // weights as B operands (N = outputs x K = inputs): the packed BF16 image, biases
+    static_assert(F_A == PK_FWD, "packed forward image = the weight region of shared memory");
+    bool ok = load_packed(sm, pk, PK_FWD, &cbar);
     float* bias = reinterpret_cast<float*>(sm + F_BIAS);
     for (int e = tid; e < 4 * NH + NOUT; e += TILE) bias[e] = e < 4 * NH ? prm[boff(e / NH + 1) + e % NH] : prm[OB5 + e - 4 * NH];
     // input tile (K = 16)
@@ -157,8 +208,7 @@ __global__ void __launch_bounds__(TILE) k_mlp_fwd(const float* __restrict__ prm,
     sync_for_mma();
     const uint32_t tmem = tslot;
     const uint32_t lane_addr = tmem + ((uint32_t)((tid >> 5) * 32) << 16);
-    bool ok = true;
-    for (int l = 1; l <= 5; ++l) {
+    for (int l = 1; l <= 5 && ok; ++l) {
         const int K = l == 1 ? NIN : NH, N = l == 5 ? NOUT : NH;
         const unsigned char* W = sm + (l == 1 ? F_W1 : l == 2 ? F_W2 : l == 3 ? F_W3 : l == 4 ? F_W4 : F_W5);
         if (tid == 0) {
@@ -198,12 +248,12 @@ __global__ void __launch_bounds__(TILE) k_mlp_fwd(const float* __restrict__ prm,
 constexpr int B_W2 = 0, B_W3 = 32768, B_W4 = 65536, B_W5 = 98304, B_A = B_W5 + 4096, B_B = B_A + 32768, B_C = B_B + 32768;
 constexpr int B_BYTES = B_C + 32768;
 
-__global__ void __launch_bounds__(TILE) k_mlp_bwd(const float* __restrict__ prm, const float* __restrict__ X,
+__global__ void __launch_bounds__(TILE) k_mlp_bwd(const unsigned char* __restrict__ pk, const float* __restrict__ X,
                                                   const float* __restrict__ Y, int P, const float* __restrict__ pred,
                                                   const float* __restrict__ Zs, float* __restrict__ gpart,
                                                   float* __restrict__ lpart, int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, cbar;
     __shared__ uint32_t tslot;
     __shared__ float red[TILE / 32];
     const int tid = threadIdx.x;
@@ -211,11 +261,9 @@ __global__ void __launch_bounds__(TILE) k_mlp_bwd(const float* __restrict__ prm,
     const bool valid = p < P;
     float* g = gpart + (size_t)blockIdx.x * NPARAM;
     if (tid < 32) tmem_alloc(&tslot, 2 * NH);
-    for (int l = 2; l <= 4; ++l) {
-        unsigned char* W = sm + (l == 2 ? B_W2 : l == 3 ? B_W3 : B_W4);
-        for (int e = tid; e < NH * NH; e += TILE) { const int n = e / NH, k = e % NH; put_bf16(W, cm(n, k, NH), prm[woff(l) + e]); }
-    }
-    for (int e = tid; e < NH * NOUT; e += TILE) { const int n = e / NOUT, k = e % NOUT; put_bf16(sm + B_W5, cm(n, k, NOUT), prm[OW5 + e]); }
+    // weights as B operands of the dH GEMMs (N = inputs x K = outputs): the packed BF16 image
+    static_assert(B_A == PK_BWD, "packed backward image = the weight region of shared memory");
+    bool ok = load_packed(sm, pk + PK_FWD, PK_BWD, &cbar);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(saddr(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -237,7 +285,6 @@ __global__ void __launch_bounds__(TILE) k_mlp_bwd(const float* __restrict__ prm,
     if (tid == 0) lpart[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
     const uint32_t tmem = tslot;
     const uint32_t lane_addr = tmem + ((uint32_t)((tid >> 5) * 32) << 16);
-    bool ok = true;
     uint32_t phase = 0;
     for (int l = 5; l >= 1 && ok; --l) {
         const int N = l == 5 ? NOUT : NH;          // outputs of layer l
@@ -359,6 +406,7 @@ struct fdlb_mlp {
     float* Zs = nullptr;
     float* pred = nullptr;
     int* err = nullptr;
+    unsigned char* pk = nullptr;      // packed BF16 weight images (k_mlp_pack)
     int max_points = 0;
     long long t = 0;
     cudaStream_t stream = nullptr;
@@ -380,6 +428,7 @@ static size_t mlp_layout(int max_points, size_t* off) {
     off[5] = o; o += al256(sizeof(float) * 4 * NH * (size_t)max_points);   // pre-activations
     off[6] = o; o += al256(sizeof(float) * NUSED * (size_t)max_points);    // predictions
     off[7] = o; o += al256(sizeof(int));
+    off[8] = o; o += al256(PK_BYTES);                            // packed BF16 weight images
     return o;
 }
 
@@ -398,7 +447,7 @@ extern "C" int32_t fdlb_mlp_param_count(void) { return NPARAM; }
 
 extern "C" size_t fdlb_mlp_workspace_bytes(int32_t max_points) {
     if (max_points < 1) return 0;
-    size_t off[8];
+    size_t off[9];
     return mlp_layout(max_points, off);
 }
 
@@ -406,7 +455,7 @@ extern "C" const char* fdlb_mlp_last_error(const fdlb_mlp* h) { return h ? h->ms
 
 extern "C" int fdlb_mlp_create(fdlb_mlp** out, void* dev_ws, size_t bytes, int32_t max_points, uint64_t seed, void* stream) {
     if (!out || !dev_ws || max_points < 1) return mlp_fail(nullptr, FDLB_EINVAL, "fdlb_mlp_create: bad arguments");
-    size_t off[8];
+    size_t off[9];
     const size_t need = mlp_layout(max_points, off);
     if (bytes < need || (reinterpret_cast<uintptr_t>(dev_ws) & 255))
         return mlp_fail(nullptr, FDLB_ENOMEM, "fdlb_mlp_create: workspace smaller than fdlb_mlp_workspace_bytes or misaligned");
@@ -420,6 +469,7 @@ extern "C" int fdlb_mlp_create(fdlb_mlp** out, void* dev_ws, size_t bytes, int32
     h->Zs = reinterpret_cast<float*>(b + off[5]);
     h->pred = reinterpret_cast<float*>(b + off[6]);
     h->err = reinterpret_cast<int*>(b + off[7]);
+    h->pk = reinterpret_cast<unsigned char*>(b + off[8]);
     h->max_points = max_points;
     h->stream = reinterpret_cast<cudaStream_t>(stream);
     int rc = mlp_cuda(h, cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, F_BYTES), "attributes");
@@ -465,7 +515,8 @@ static int check_err(fdlb_mlp* h) {
 extern "C" int fdlb_mlp_predict(fdlb_mlp* h, const float* dev_x, int32_t points, float* dev_y) {
     if (!h || !dev_x || !dev_y || points < 1) return mlp_fail(h, FDLB_EINVAL, "fdlb_mlp_predict: bad arguments");
     const int nblk = (points + TILE - 1) / TILE;
-    k_mlp_fwd<<<nblk, TILE, F_BYTES, h->stream>>>(h->prm, dev_x, points, dev_y, nullptr, h->err);
+    k_mlp_pack<<<(NPARAM + 255) / 256, 256, 0, h->stream>>>(h->prm, h->pk);
+    k_mlp_fwd<<<nblk, TILE, F_BYTES, h->stream>>>(h->prm, h->pk, dev_x, points, dev_y, nullptr, h->err);
     int rc = mlp_cuda(h, cudaGetLastError(), "forward kernel");
     if (!rc) rc = check_err(h);
     return rc;
@@ -476,8 +527,9 @@ extern "C" int fdlb_mlp_train_step(fdlb_mlp* h, const float* dev_x, const float*
     if (!h || !dev_x || !dev_y || points < 1 || points > h->max_points || !(lr >= 0.0f))
         return mlp_fail(h, FDLB_EINVAL, "fdlb_mlp_train_step: bad arguments (points must be <= max_points)");
     const int nblk = (points + TILE - 1) / TILE;
-    k_mlp_fwd<<<nblk, TILE, F_BYTES, h->stream>>>(h->prm, dev_x, points, h->pred, h->Zs, h->err);
-    k_mlp_bwd<<<nblk, TILE, B_BYTES, h->stream>>>(h->prm, dev_x, dev_y, points, h->pred, h->Zs, h->gpart, h->lpart, h->err);
+    k_mlp_pack<<<(NPARAM + 255) / 256, 256, 0, h->stream>>>(h->prm, h->pk);
+    k_mlp_fwd<<<nblk, TILE, F_BYTES, h->stream>>>(h->prm, h->pk, dev_x, points, h->pred, h->Zs, h->err);
+    k_mlp_bwd<<<nblk, TILE, B_BYTES, h->stream>>>(h->pk, dev_x, dev_y, points, h->pred, h->Zs, h->gpart, h->lpart, h->err);
     if (lr > 0.0f) h->t += 1;
     const float b1t = lr > 0.0f ? (float)std::pow(0.9, (double)h->t) : 0.0f;
     const float b2t = lr > 0.0f ? (float)std::pow(0.999, (double)h->t) : 0.0f;

@@ -17,7 +17,22 @@ def inputs(P, seed):
     return X
 
 
+def forward_scale(theta, X):
+    """Per output, the sum of the magnitudes of the terms of its last-layer sum (bias included),
+    with the oracle's BF16-rounded operands: the scale of the FP32 accumulation error."""
+    _, (hs, _) = omlp.forward_bf16(theta, X)
+    W5, b5 = omlp.unpack(theta)[4]
+    return (np.abs(hs[4]) @ np.abs(omlp.bf16(W5)) + np.abs(b5))[:, :3]
+
+
 def test_forward_matches_oracle():
+    """Element-wise against the oracle with BF16 operands where the kernel rounds them.  What
+    remains is the FP32 accumulation (~K eps_32 of the sum of |terms| per layer, K <= 128) and,
+    rarely, a hidden activation whose FP32 and FP64 values round to neighbouring BF16 numbers
+    (one BF16 ulp, 2^-8 relative, of one term).  Each output depends on 4 x 128 rounded
+    activations, so a few outputs in a thousand carry such a neighbour (measured 0.6 %).  Bar per
+    output: 2e-3 of its scale, and at most 2 % of the outputs beyond 2e-4 of it; a transposed or
+    misplaced block errs by O(1) of the scale everywhere."""
     import torch
     F = lib()
     net = F.MLP(max_points=1000, seed=5)
@@ -25,12 +40,20 @@ def test_forward_matches_oracle():
     assert theta.size == omlp.n_params()
     X = inputs(333, 1)                          # ragged last tile
     y = net.predict(torch.tensor(X, device="cuda")).cpu().numpy()
-    ref, _ = omlp.forward(theta, X.astype(np.float64))
-    err = np.abs(y - ref).max() / np.abs(ref).max()
-    assert err < 3e-2, err                      # BF16 operands, FP32 accumulation
+    ref, _ = omlp.forward_bf16(theta, X.astype(np.float64))
+    rel = np.abs(y - ref) / forward_scale(theta, X.astype(np.float64))
+    print("forward: max err / scale", rel.max(), "fraction > 2e-4", np.mean(rel > 2e-4))
+    assert rel.max() < 2e-3, rel.max()
+    assert np.mean(rel > 2e-4) < 2e-2
+    # and the plain FP64 network, for scale: BF16 operands cost ~1e-2
+    ref64, _ = omlp.forward(theta, X.astype(np.float64))
+    assert np.abs(y - ref64).max() / np.abs(ref64).max() < 3e-2
 
 
 def test_gradient_matches_oracle():
+    """Every gradient element against the BF16-operand oracle, relative to the sum of the
+    magnitudes of its terms (the FP32 accumulation bound), with the same allowance for rare
+    BF16 rounding neighbours as the forward pass.  A transposed or shifted block fails this."""
     import torch
     F = lib()
     net = F.MLP(max_points=512, seed=9)
@@ -43,16 +66,19 @@ def test_gradient_matches_oracle():
     X = inputs(300, 3)
     Y = rng.normal(0, 0.5, (300, 3)).astype(np.float32)
     loss, g = net.train_step(torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"), lr=0.0, want_grad=True)
-    rl, rg = omlp.loss_and_grad(theta, X.astype(np.float64), Y.astype(np.float64))
-    assert abs(loss - rl) < 2e-2 * rl
+    rl, rg, sc = omlp.loss_and_grad_bf16(theta, X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss - rl) < 1e-4 * rl
     g = g.cpu().numpy().astype(np.float64)
-    cos = g @ rg / (np.linalg.norm(g) * np.linalg.norm(rg))
-    rel = np.linalg.norm(g - rg) / np.linalg.norm(rg)
-    assert cos > 0.999 and rel < 5e-2, (cos, rel)
-    # per layer as well
-    for (gw, gb), (rw, rb) in zip(omlp.unpack(g), omlp.unpack(rg)):
-        assert np.linalg.norm(gw - rw) <= 6e-2 * np.linalg.norm(rw) + 1e-9
+    live = sc > 0
+    rel = np.abs(g - rg)[live] / sc[live]
+    print("gradient: max err / scale", rel.max(), "fraction > 2e-4", np.mean(rel > 2e-4))
+    assert rel.max() < 2e-2, rel.max()
+    assert np.mean(rel > 2e-4) < 5e-3
+    assert np.all(g[~live] == 0.0)
     assert np.all(omlp.unpack(g)[4][0][:, 3:] == 0.0)
+    # the FP64 network's gradient, for scale
+    _, rg64 = omlp.loss_and_grad(theta, X.astype(np.float64), Y.astype(np.float64))
+    assert np.linalg.norm(g - rg64) < 5e-2 * np.linalg.norm(rg64)
 
 
 def test_training_lowers_the_loss():
