@@ -430,6 +430,12 @@ __device__ void finalize_tile(const Inst& I, int i0, const double* ss, int tid) 
     }
 }
 
+// Programmatic dependent launch: a stepping kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream drains; it waits here, before
+// reading anything, until the predecessor has completed and its writes are visible (a no-op
+// for a kernel launched without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Named barrier over `n` threads (moment finalisation runs on 128-thread parts of a block).
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
@@ -1035,6 +1041,7 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
 template <int QB>
 __global__ void __launch_bounds__(TILE * NOD_WARPS) k_nodal(const Inst* __restrict__ insts, const Work* __restrict__ work) {
     extern __shared__ __align__(16) double nsm[];
+    pdl_wait();
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE || I.smem_res) return;
@@ -1163,6 +1170,7 @@ __device__ void resid_item(Inst& I, int idx, double tol, double* resid_all) {
 
 
 __global__ void __launch_bounds__(256) k_resid(Inst* insts, int anchor, double tol, double* resid_all) {
+    pdl_wait();
     Inst& I = insts[blockIdx.x];
     const int ld = I.ld, N = I.N;
     double* nd = I.node;
@@ -1727,6 +1735,7 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
 template <typename S, typename C>
 __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restrict__ insts, const Work* __restrict__ work, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE || I.smem_res) return;
@@ -1900,6 +1909,23 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_smemres(Inst* insts, const i
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
+// The stepping kernels (closure, update, residual) are launched with programmatic stream
+// serialization: the next kernel of a step is set up while the previous one finishes.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Kernel attributes (dynamic shared memory above 48 KB, non-portable cluster sizes) and the
 // __constant__ tables are per device: each device keeps its own record of what was set, and
 // a mutex serialises the updates.  Attributes only ever grow, so contexts created earlier on
@@ -1971,8 +1997,11 @@ cudaError_t launch_moments(const Inst* d_inst, const Work* d_upd, int n_upd, int
 }
 
 cudaError_t launch_resid(const Inst* d_inst, int count, int anchor_inst, double freeze_tol, double* d_resid_all, cudaStream_t s) {
-    k_resid<<<count, 256, 0, s>>>(const_cast<Inst*>(d_inst), anchor_inst, freeze_tol, d_resid_all);
-    return cudaGetLastError();
+    if (anchor_inst != -2) {
+        k_resid<<<count, 256, 0, s>>>(const_cast<Inst*>(d_inst), anchor_inst, freeze_tol, d_resid_all);
+        return cudaGetLastError();
+    }
+    return launch_pdl(k_resid, (unsigned)count, dim3(256), 0, s, const_cast<Inst*>(d_inst), anchor_inst, freeze_tol, d_resid_all);
 }
 
 // (the caller holds g_attr_mu)
@@ -1991,9 +2020,8 @@ static cudaError_t set_smem(DevAttr* A, size_t smem64, size_t smem32) {
 
 cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int qmax, cudaStream_t s) {
     const size_t smem = (size_t)nodal_smem_doubles(qmax) * sizeof(double);
-    if (qmax <= 8) k_nodal<8><<<n_nod, TILE * NOD_WARPS, smem, s>>>(d_inst, d_nod);
-    else k_nodal<QMAX><<<n_nod, TILE * NOD_WARPS, smem, s>>>(d_inst, d_nod);
-    return cudaGetLastError();
+    if (qmax <= 8) return launch_pdl(k_nodal<8>, (unsigned)n_nod, dim3(TILE * NOD_WARPS), smem, s, d_inst, d_nod);
+    return launch_pdl(k_nodal<QMAX>, (unsigned)n_nod, dim3(TILE * NOD_WARPS), smem, s, d_inst, d_nod);
 }
 
 cudaError_t prepare_kernels(size_t smem64, size_t smem32, int qmax) {
@@ -2135,9 +2163,10 @@ cudaError_t launch_smemres(Inst* d_inst, const int* d_list, int n, int qmax, siz
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
                           bool f64, bool f32, cudaStream_t s) {
     dim3 blk(TILE, UPD_WARPS);
-    if (f64) k_update<double, double><<<n_upd, blk, smem64, s>>>(d_inst, d_upd, stage);
-    if (f32) k_update<float, float><<<n_upd, blk, smem32, s>>>(d_inst, d_upd, stage);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (f64) e = launch_pdl(k_update<double, double>, (unsigned)n_upd, blk, smem64, s, d_inst, d_upd, stage);
+    if (e == cudaSuccess && f32) e = launch_pdl(k_update<float, float>, (unsigned)n_upd, blk, smem32, s, d_inst, d_upd, stage);
+    return e;
 }
 
 }  // namespace fdlb
