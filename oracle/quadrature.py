@@ -228,7 +228,9 @@ def project_full(nodes: np.ndarray, u, T, amax: int = 3) -> np.ndarray:
     p = u + sqrt(T) y and an AUX_FULL-point Gauss-Hermite rule in y."""
     u = np.asarray(u, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
-    aux = full_range_rule(AUX_FULL)
+    # the integrand is a polynomial of degree len(nodes) - 1 + amax times the rule's weight:
+    # exact once 2 M - 1 reaches that degree (AUX_FULL points at least)
+    aux = full_range_rule(max(AUX_FULL, (len(nodes) + amax) // 2 + 1))
     y = aux.nodes.reshape((-1,) + (1,) * u.ndim)
     W = aux.weights.reshape((-1,) + (1,) * u.ndim)
     x = u + np.sqrt(T) * y

@@ -327,7 +327,8 @@ int validate(const fdlb_params& p, std::string& why) {
     auto bad = [&](const char* m) { why = m; return FDLB_EINVAL; };
     if (p.struct_size != sizeof(fdlb_params)) return bad("struct_size != sizeof(fdlb_params)");
     if (p.nx < 8 || p.nx > 4096) return bad("nx must be in [8, 4096]");
-    if (p.qx_half < 1 || p.qx_half > QMAX) return bad("qx_half must be in [1, 16]");
+    if (p.qx_half < 1) return bad("qx_half must be >= 1");
+    if (p.x_quadrature == FDLB_XQ_HALF && p.qx_half > QX_HALF_MAX) return bad("qx_half must be in [1, 32] (half-range x)");
     if (p.qy != 0 && (p.qy < 2 || p.qy > QYMAX)) return bad("qy must be 0 or in [2, 8]");
     if (p.qz != 0 && (p.qz < 3 || p.qz > QZMAX)) return bad("qz must be 0 or in [3, 8]");
     if (p.qy == 0 && p.qz != 0) return bad("qy == 0 (1D reduced) requires qz == 0");
@@ -341,8 +342,8 @@ int validate(const fdlb_params& p, std::string& why) {
     if (p.chi_model != FDLB_CHI_SET && p.chi_model != FDLB_CHI_RET_FM) return bad("unknown chi_model");
     if (p.chi_model == FDLB_CHI_RET_FM && !(p.eta0 > 0)) return bad("chi_model RET-FM needs eta0 > 0");
     if (p.x_quadrature != FDLB_XQ_HALF && p.x_quadrature != FDLB_XQ_FULL) return bad("unknown x_quadrature");
-    if (p.x_quadrature == FDLB_XQ_FULL && p.qx_half > QMAX / 2)
-        return bad("the full-range x quadrature needs qx_half <= 8 (order 2 qx_half <= 16)");
+    if (p.x_quadrature == FDLB_XQ_FULL && p.qx_half > QX_FULL_MAX)
+        return bad("the full-range x quadrature needs qx_half <= 100 (order 2 qx_half <= 200)");
     if (!(p.kn > 0) || !std::isfinite(p.kn)) return bad("kn must be > 0");
     if (!(p.eta0 >= 0 && p.eta0 < 0.5)) return bad("eta0 must be in [0, 0.5)");
     if (!(p.T_left > 0) || !(p.T_right > 0)) return bad("wall temperatures must be > 0");
@@ -387,7 +388,7 @@ void fm_weights(const fdlb_params& p, std::vector<int>& ptr, std::vector<int>& c
 // Byte layout of one instance inside the workspace.
 struct Layout {
     size_t tables = 0, fbuf = 0, node = 0, tab = 0, tab32 = 0, misc = 0, msum = 0, mcnt = 0, total = 0;
-    int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, My = 0, Mz = 0, groups = 1, ukc = 1;
+    int ld = 0, K = 0, Tc = 0, form = 0, ntab = 0, trows = 0, My = 0, Mz = 0, groups = 1, ukc = 1;
     int fm_nnz = 0;            // entries of the Fischer-Methfessel weights (RET-FM only)
 };
 
@@ -440,7 +441,8 @@ Layout layout_of(const fdlb_params& p, int ukc) {
     size_t nd = 0;
     // tables (doubles), each padded to 256 B
     auto add = [&](size_t n) { nd += al256(n * 8) / 8; };
-    add(2 * Q); add(MX); add(MX); add(MX8); add(MX8); add(Lx); add(Lx + 1); add(Lx + 1); add(Lx * Q);
+    const int mxa = std::max(MX, p.x_quadrature == FDLB_XQ_FULL ? Q + 2 : aux_points_half(Lx));   // aux x rule
+    add(2 * Q); add(mxa); add(mxa); add(MX8); add(MX8); add(Lx); add(Lx + 1); add(Lx + 1); add(Lx * Q);
     add(QYMAX); add(MYMAX); add(MYMAX); add(QYMAX * QYMAX);
     add(QZMAX); add(MYMAX); add(MYMAX); add(QZMAX * QZMAX);
     add(QYMAX * QYMAX);
@@ -454,7 +456,7 @@ Layout layout_of(const fdlb_params& p, int ukc) {
     if (f32) {
         add32(2 * Q); add32(p.nx); add32(QYMAX * QYMAX); add32(L.K); add32(L.K);
         // float pairs: xq, xw, xq8, xw8, xa, xb, xib, xH, yq, yw, yH, zq, zw, zH, fsq, fisq
-        add32(2 * MX); add32(2 * MX); add32(2 * MX8); add32(2 * MX8); add32(2 * Lx); add32(2 * (Lx + 1));
+        add32(2 * mxa); add32(2 * mxa); add32(2 * MX8); add32(2 * MX8); add32(2 * Lx); add32(2 * (Lx + 1));
         add32(2 * (Lx + 1)); add32(2 * Lx * Q); add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QYMAX * QYMAX);
         add32(2 * MYMAX); add32(2 * MYMAX); add32(2 * QZMAX * QZMAX); add32(2 * (QYMAX + 2)); add32(2 * (QYMAX + 2));
         add32(2 * 2 * Q);   // px pairs
@@ -474,12 +476,18 @@ Layout layout_of(const fdlb_params& p, int ukc) {
     L.misc = al256(8 * 8);
     L.tab32 = f32 ? al256((size_t)L.ntab * L.ld * 4) : 0;
     L.ukc = std::min(L.K, ukc);
-    // the update block stages its chunk's rows in shared memory: halve the chunk of the largest
-    // velocity sets until a block fits in the per-block limit (with room for the static part)
+    // the update block stages its chunk's rows and the table rows it uses in shared memory:
+    // halve the chunk of the largest velocity sets until a block fits in the per-block limit
+    // (with room for the static part)
+    auto trows = [&](int kc) {
+        const int nkx = std::min(2 * p.qx_half, (kc + L.Tc - 1) / L.Tc + 1);   // x-velocities a chunk spans
+        return std::min(L.ntab, 4 * nkx + 4 * L.Tc + 1);
+    };
     {
         const size_t s_max = p.precision == FDLB_FP32_STORAGE ? 4 : 8;
-        while (L.ukc > 8 && update_smem_bytes(L.ntab, L.ukc, s_max, s_max) > UPD_SMEM_LIMIT) L.ukc = (L.ukc + 1) / 2;
+        while (L.ukc > 8 && update_smem_bytes(trows(L.ukc), L.ukc, s_max, s_max) > UPD_SMEM_LIMIT) L.ukc = (L.ukc + 1) / 2;
     }
+    L.trows = trows(L.ukc);
     L.groups = (L.K + L.ukc - 1) / L.ukc;
     L.msum = L.groups > 1 ? al256((size_t)L.groups * MOM_SUMS * L.ld * 8) : 0;
     L.mcnt = al256((size_t)(L.ld / TILE) * 4);
@@ -571,11 +579,11 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         Inst I;
         std::memset(&I, 0, sizeof(I));
         I.N = N; I.ld = L.ld; I.Q = Q; I.Qy = p.qy; I.Qz = p.qz; I.form = L.form; I.Tc = L.Tc; I.K = L.K;
-        I.Mx = MX; I.My = L.My; I.Mz = L.Mz;
+        I.Mx = aux_points_half(p.x_quadrature == FDLB_XQ_FULL ? 2 * p.qx_half : p.qx_half); I.My = L.My; I.Mz = L.Mz;
         I.precision = p.precision == FDLB_FP64 ? FDLB_FP64 : FDLB_FP32_STORAGE;
         I.two_phase = p.precision == FDLB_FP32_THEN_FP64;
         I.j1_shear = p.j1_shear;
-        I.chi_model = p.chi_model; I.ntab = L.ntab; I.mgroups = L.groups; I.ukc = L.ukc;
+        I.chi_model = p.chi_model; I.ntab = L.ntab; I.trows = L.trows; I.mgroups = L.groups; I.ukc = L.ukc;
         {
             const uint64_t h = params_fnv(p, true);
             I.sr_key = (uint32_t)(h ^ (h >> 32));
@@ -619,12 +627,13 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         // positive nodes (the upper half of its ascending list) play the same part
         Rule xr = xfull ? make_rule(1, Lx) : make_rule(0, Q);
         const int kpos = xfull ? Q : 0;            // index of +p_1 in xr.x
-        Rule xa = xfull ? make_rule(1, I.Mx) : make_rule(0, MX);
+        Rule xa = make_rule(xfull ? 1 : 0, I.Mx);
+        const int mxa = std::max(MX, I.Mx);
         {
             double* h = put(&I.px, 2 * Q);
             for (int k = 0; k < Q; ++k) { h[k] = xr.x[kpos + k]; h[Q + k] = -xr.x[kpos + k]; }
-            h = put(&I.xq, MX); for (int m = 0; m < I.Mx; ++m) h[m] = xa.x[m];
-            h = put(&I.xw, MX); for (int m = 0; m < I.Mx; ++m) h[m] = xa.w[m];
+            h = put(&I.xq, mxa); for (int m = 0; m < I.Mx; ++m) h[m] = xa.x[m];
+            h = put(&I.xw, mxa); for (int m = 0; m < I.Mx; ++m) h[m] = xa.w[m];
             Rule xa8 = make_rule(0, MX8);
             h = put(&I.xq8, MX8); for (int m = 0; m < MX8; ++m) h[m] = xa8.x[m];
             h = put(&I.xw8, MX8); for (int m = 0; m < MX8; ++m) h[m] = xa8.w[m];
@@ -772,8 +781,8 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
                     h2[2 * k + 1] = (float)(src[k] - (double)hi);
                 }
             };
-            pairs(&I.xq2, I.xq, MX);
-            pairs(&I.xw2, I.xw, MX);
+            pairs(&I.xq2, I.xq, std::max(MX, I.Mx));
+            pairs(&I.xw2, I.xw, std::max(MX, I.Mx));
             pairs(&I.xq82, I.xq8, MX8);
             pairs(&I.xw82, I.xw8, MX8);
             pairs(&I.xa2, I.xa, Lx);
@@ -831,8 +840,8 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         }
         c->qmax = std::max(c->qmax, Lx);      // register and shared arrays hold Lx polynomials
         c->ukc_max = std::max(c->ukc_max, L.ukc);
-        if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, update_smem_bytes(L.ntab, L.ukc, 8, 8)), c->any_fp64 = true;
-        if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, update_smem_bytes(L.ntab, L.ukc, 4, 4)), c->any_fp32 = true;
+        if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, update_smem_bytes(L.trows, L.ukc, 8, 8)), c->any_fp64 = true;
+        if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, update_smem_bytes(L.trows, L.ukc, 4, 4)), c->any_fp32 = true;
     }
     if (off > need) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: workspace layout overflow"); }
     c->smem_upd_f64 = max_smem64;
@@ -960,7 +969,7 @@ static void choose_smem_resident(fdlb_ctx* c) {
         const Inst& I = c->inst[i];
         if (I.two_phase) continue;
         const size_t sz = I.precision == FDLB_FP32_STORAGE ? 4 : 8;
-        const size_t upd = update_smem_bytes(I.ntab, I.ukc, sz, sz);
+        const size_t upd = update_smem_bytes(I.trows, I.ukc, sz, sz);
         const size_t fb = smemres_buffer_bytes(I.K, I.ld, sz);
         const size_t need = smemres_scratch_bytes(I.Lx, upd) + 3 * fb;
         if (need <= limit) cand.push_back({i, I.Lx, upd, fb, need});

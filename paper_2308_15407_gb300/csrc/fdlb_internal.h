@@ -7,11 +7,18 @@
 
 namespace fdlb {
 
-constexpr int QMAX = 16;        // half-range order per side
+constexpr int QMAX = 16;        // x polynomials per block of the x projections (register block)
+constexpr int QX_HALF_MAX = 32; // half-range order per side, at most
+constexpr int QX_FULL_MAX = 100;  // half the full-range x order (order 2 x 100 = 200), at most
+constexpr int LXMAX = 2 * QX_FULL_MAX;  // orthonormal x polynomials of a projection, at most
 constexpr int QYMAX = 8;        // full-range order on y
 constexpr int QZMAX = 8;        // full-range order on z
 constexpr int TCMAX = QYMAX * QZMAX;
-constexpr int MX = 16;          // auxiliary half-range rule used for the x projections
+constexpr int MX = 16;          // auxiliary half-range rule of the x projections, at least
+// Points of the auxiliary half-range rule for Lx half-range polynomials: the integrand is a
+// polynomial of degree Lx + 2 times exp(q v - v^2/2); 16 points up to Lx = 16, beyond that
+// enough for exactness on the polynomial part with the same margin for the exponential.
+__host__ __device__ inline int aux_points_half(int Lx) { return Lx <= 16 ? MX : (Lx + 21) / 2; }
 constexpr int MX8 = 8;          // shorter auxiliary rule when |u_x|/sqrt(T) is small (see k_nodal)
 constexpr int MYMAX = 8;        // auxiliary full-range rule (exact: 2M > Q + 2)
 constexpr int NTERMS = 13;      // monomials of f^S + tau J1
@@ -49,6 +56,8 @@ struct Inst {
     int Lx;                    // orthonormal x polynomials in the projection: Q (half), 2Q (full)
     int two_phase;             // FDLB_FP32_THEN_FP64: tables and buffers exist for both storages
     int ntab;                  // doubles per node in the projection table
+    int trows;                 // rows of an update block's compact table: 4 NKX x-projection rows
+                               // (the chunk's x-velocities), 4 Tc transverse rows, 1/tau
     uint32_t sr_key;           // hash of the parameters: seeds the stochastic rounding of FP32 storage
     int ukc;                   // velocities per update block (chunk) of a tile
     int mgroups;               // update chunks per tile (> 1: partial moment sums in msum)
@@ -59,7 +68,7 @@ struct Inst {
     // tables
     const double* px;          // [2Q]: +p_1..+p_Q, -p_1..-p_Q
     const double* xq;          // [Mx] aux nodes: half-range rule (half), Gauss-Hermite rule (full)
-    const double* xw;          // [Mx] aux weights
+    const double* xw;          // [Mx] aux weights (Mx = aux_points_half(Lx) or Q + 2)
     const double* xq8;         // [MX8] 8-point aux half-range nodes
     const double* xw8;         // [MX8] 8-point aux half-range weights
     const double* xa;          // [Lx]   recurrence alpha_l

@@ -61,36 +61,49 @@ __device__ __forceinline__ double chi_cs(double eta) {
 __device__ void proj_x(const Inst& I, double u, double T, int half, double* out, int stride) {
     const int Q = I.Q, Lx = I.Lx;
     const bool full = I.xfull;
-    double G[4][QMAX];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-        for (int l = 0; l < QMAX; ++l) G[a][l] = 0.0;
     const double uu = half ? -u : u;
     const double sT = sqrt(T), v = uu / sT, ev = -0.5 * v * v;
-    const int M = full ? I.Mx : MX;
-    for (int m = 0; m < M; ++m) {
-        const double q = I.xq[m];
-        const double x = full ? fma(sT, q, uu) : sT * q;
-        const double E = full ? I.xw[m] : I.xw[m] * exp(fma(q, v, ev));
-        const double y = full ? sT * q : x - uu;
-        const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
-        double hm = 0.0, h = I.x_h0;
-        for (int l = 0; l < Lx; ++l) {
-            G[0][l] = fma(E, h, G[0][l]);
-            G[1][l] = fma(e1, h, G[1][l]);
-            G[2][l] = fma(e2, h, G[2][l]);
-            G[3][l] = fma(e3, h, G[3][l]);
-            const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
-            hm = h;
-            h = hn;
+    const int M = I.Mx;
+    // the polynomials in blocks of QMAX; the H products continue one chain across blocks
+    // (kept in out, signed at the end)
+    for (int lb = 0; lb < Lx; lb += QMAX) {
+        const int nl = min(QMAX, Lx - lb);
+        double G[4][QMAX];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            for (int l = 0; l < QMAX; ++l) G[a][l] = 0.0;
+        for (int m = 0; m < M; ++m) {
+            const double q = I.xq[m];
+            const double x = full ? fma(sT, q, uu) : sT * q;
+            const double E = full ? I.xw[m] : I.xw[m] * exp(fma(q, v, ev));
+            const double y = full ? sT * q : x - uu;
+            const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+            double hm = 0.0, h = I.x_h0;
+            for (int l = 0; l < lb; ++l) {
+                const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
+                hm = h;
+                h = hn;
+            }
+            for (int j = 0; j < nl; ++j) {
+                const int l = lb + j;
+                G[0][j] = fma(E, h, G[0][j]);
+                G[1][j] = fma(e1, h, G[1][j]);
+                G[2][j] = fma(e2, h, G[2][j]);
+                G[3][j] = fma(e3, h, G[3][j]);
+                const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
+                hm = h;
+                h = hn;
+            }
         }
-    }
-    for (int a = 0; a < 4; ++a) {
-        const double sgn = (half && (a & 1)) ? -1.0 : 1.0;
-        for (int k = 0; k < Q; ++k) {
-            double s = 0.0;
-            for (int l = 0; l < Lx; ++l) s = fma(I.xH[l * Q + k], G[a][l], s);
-            out[(a * 2 * Q + half * Q + k) * stride] = sgn * s;
+        const bool last = lb + nl == Lx;
+        for (int a = 0; a < 4; ++a) {
+            const double sgn = (half && (a & 1)) ? -1.0 : 1.0;
+            for (int k = 0; k < Q; ++k) {
+                double* o = out + (a * 2 * Q + half * Q + k) * stride;
+                double s = lb == 0 ? 0.0 : *o;
+                for (int j = 0; j < nl; ++j) s = fma(I.xH[(lb + j) * Q + k], G[a][j], s);
+                *o = last ? sgn * s : s;
+            }
         }
     }
 }
@@ -192,7 +205,7 @@ __device__ void build_Y(const Inst& I, const double* c, double uy, double T, dou
 // set-up: wall Maxwellians, initial state
 // ---------------------------------------------------------------------------
 __device__ void wall_maxwellian(const Inst& I, double U, double T, double* g) {
-    double Px[4 * 2 * QMAX];
+    double Px[4 * 2 * QX_FULL_MAX];
     proj_x(I, 0.0, T, 0, Px, 1);
     proj_x(I, 0.0, T, 1, Px, 1);
     double c[NTERMS];
@@ -523,6 +536,7 @@ __device__ void moments_final_tile(const Inst& I, int i0, double* ss, int tid, i
 constexpr int CL_ROWS = 5 + 8 + 15;    // closure item: gradients, scalars, coefficients
 
 __host__ __device__ inline int nodal_smem_doubles(int qmax) {
+    if (qmax > QMAX) qmax = QMAX;                // larger x orders run in blocks of QMAX polynomials
     const int r01 = (NOD_WARPS + 1) * 4 * qmax * TILE;
     const int r2 = (CL_ROWS + 4 * QYMAX + 3 * QZMAX + 8 * QYMAX + 2 * MYMAX * (QYMAX + 1)) * TILE;
     return r01 > r2 ? r01 : r2;
@@ -582,71 +596,90 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
     const bool full = I.xfull;               // full-range x: as in the FP64 branch
     const int Lx = I.Lx;
     const bool short_rule = !full && use_short == 1 && Q <= 12;
-    const int M = full ? I.Mx : (short_rule ? MX8 : MX);
+    const int M = full ? I.Mx : (short_rule ? MX8 : I.Mx);
     const df sT = df_of(xs[0][lane]), uu = df_of(xs[1][lane]), v = df_of(xs[2][lane]), hv2 = df_of(xs[3][lane]);
-    df G[4][QB];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int l = 0; l < QB; ++l) G[a][l] = {0.0f, 0.0f};
     const df one = {1.0f, 0.0f};
-    for (int m = wid; m < M; m += NOD_WARPS) {
-        const df q = df_of(short_rule ? I.xq82[m] : I.xq2[m]);
-        const df Wm = df_of(short_rule ? I.xw82[m] : I.xw2[m]);
-        df x, E, y;
-        if (full) {
-            y = sT * q;
-            x = uu + y;
-            E = Wm;
-        } else {
-            const df z = q * v - hv2;
-            df ez;
-            if (short_rule) {
-                ez = one;
+    float2* part = reinterpret_cast<float2*>(nsm);                  // [NOD_WARPS][4 nl][32]
+    // blocks of QB polynomials as in the FP64 branch; the chain of H products continues across
+    // blocks as float pairs in the instance's FP64 table rows (8 bytes each), and the last
+    // block rounds it into the FP32 table
+    float2* acc = reinterpret_cast<float2*>(I.tab);
+    for (int lb = 0; lb < Lx; lb += QB) {
+        const int nl = min(QB, Lx - lb);
+        float2* sum = part + NOD_WARPS * 4 * nl * TILE;             // [4 nl][32]
+        df G[4][QB];
 #pragma unroll
-                for (int j = 12; j >= 1; --j) ez = ez * z * df_of(c_inv2[j]) + one;
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int l = 0; l < QB; ++l) G[a][l] = {0.0f, 0.0f};
+        for (int m = wid; m < M; m += NOD_WARPS) {
+            const df q = df_of(short_rule ? I.xq82[m] : I.xq2[m]);
+            const df Wm = df_of(short_rule ? I.xw82[m] : I.xw2[m]);
+            df x, E, y;
+            if (full) {
+                y = sT * q;
+                x = uu + y;
+                E = Wm;
             } else {
-                ez = df_exp(z);
-            }
-            x = sT * q;
-            E = Wm * ez;
-            y = x - uu;
-        }
-        const df e1 = E * y, e2 = e1 * y, e3 = e2 * y;
-        df hm = {0.0f, 0.0f}, h = df_of(I.x_h02);
+                const df z = q * v - hv2;
+                df ez;
+                if (short_rule) {
+                    ez = one;
 #pragma unroll
-        for (int l = 0; l < QB; ++l) {
-            if (l < Lx) {
-                G[0][l] = E * h + G[0][l];
-                G[1][l] = e1 * h + G[1][l];
-                G[2][l] = e2 * h + G[2][l];
-                G[3][l] = e3 * h + G[3][l];
+                    for (int j = 12; j >= 1; --j) ez = ez * z * df_of(c_inv2[j]) + one;
+                } else {
+                    ez = df_exp(z);
+                }
+                x = sT * q;
+                E = Wm * ez;
+                y = x - uu;
+            }
+            const df e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+            df hm = {0.0f, 0.0f}, h = df_of(I.x_h02);
+            for (int l = 0; l < lb; ++l) {
                 const df hn = ((x - df_of(I.xa2[l])) * h - df_of(I.xb2[l]) * hm) * df_of(I.xib2[l + 1]);
                 hm = h;
                 h = hn;
             }
+#pragma unroll
+            for (int j = 0; j < QB; ++j) {
+                if (j < nl) {
+                    const int l = lb + j;
+                    G[0][j] = E * h + G[0][j];
+                    G[1][j] = e1 * h + G[1][j];
+                    G[2][j] = e2 * h + G[2][j];
+                    G[3][j] = e3 * h + G[3][j];
+                    const df hn = ((x - df_of(I.xa2[l])) * h - df_of(I.xb2[l]) * hm) * df_of(I.xib2[l + 1]);
+                    hm = h;
+                    h = hn;
+                }
+            }
         }
-    }
-    float2* part = reinterpret_cast<float2*>(nsm);                  // [NOD_WARPS][4 Lx][32]
-    float2* sum = part + NOD_WARPS * 4 * Lx * TILE;                 // [4 Lx][32]
+        if (lb > 0) __syncthreads();              // the previous block's readers of part and sum are done
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int l = 0; l < QB; ++l)
-            if (l < Lx) part[((wid * 4 + a) * Lx + l) * TILE + lane] = make_float2(G[a][l].hi, G[a][l].lo);
-    __syncthreads();
-    for (int r = wid; r < 4 * Lx; r += NOD_WARPS) {
-        df t = {0.0f, 0.0f};
-        for (int q = 0; q < NOD_WARPS; ++q) t = t + df_of(part[(q * 4 * Lx + r) * TILE + lane]);
-        sum[r * TILE + lane] = make_float2(t.hi, t.lo);
-    }
-    __syncthreads();
-    for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
-        const int a = o / Q, k = o - a * Q;
-        df t = {0.0f, 0.0f};
-        for (int l = 0; l < Lx; ++l) t = df_of(I.xH2[l * Q + k]) * df_of(sum[(a * Lx + l) * TILE + lane]) + t;
-        if (role && (a & 1)) t = -t;
-        if (valid) I.tab32[(size_t)(a * 2 * Q + role * Q + k) * ld + i] = df_float(t);
+            for (int j = 0; j < QB; ++j)
+                if (j < nl) part[((wid * 4 + a) * nl + j) * TILE + lane] = make_float2(G[a][j].hi, G[a][j].lo);
+        __syncthreads();
+        for (int r = wid; r < 4 * nl; r += NOD_WARPS) {
+            df t = {0.0f, 0.0f};
+            for (int q = 0; q < NOD_WARPS; ++q) t = t + df_of(part[(q * 4 * nl + r) * TILE + lane]);
+            sum[r * TILE + lane] = make_float2(t.hi, t.lo);
+        }
+        __syncthreads();
+        const bool last = lb + nl == Lx;
+        for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
+            const int a = o / Q, k = o - a * Q;
+            const size_t r = (size_t)(a * 2 * Q + role * Q + k) * ld + i;
+            df t = (lb > 0 && valid) ? df_of(acc[r]) : df{0.0f, 0.0f};
+            for (int j = 0; j < nl; ++j) t = df_of(I.xH2[(lb + j) * Q + k]) * df_of(sum[(a * nl + j) * TILE + lane]) + t;
+            if (last && role && (a & 1)) t = -t;
+            if (valid) {
+                if (last) I.tab32[r] = df_float(t);
+                else acc[r] = make_float2(t.hi, t.lo);
+            }
+        }
     }
 }
 
@@ -964,72 +997,86 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
         const bool full = I.xfull;
         const int Lx = I.Lx;
         const bool short_rule = !full && use_short == 1 && Q <= 12;
-        const int M = full ? I.Mx : (short_rule ? MX8 : MX);
-        double G[4][QB];
+        const int M = full ? I.Mx : (short_rule ? MX8 : I.Mx);
+        double* part = nsm;                                  // [NOD_WARPS][4 nl][32]
+        // the polynomials in blocks of QB: per block the sums over the auxiliary points (the
+        // recurrence run from l = 0 again), then the H products, whose chain continues across
+        // blocks in the instance's FP64 table rows (signed and written at the last block)
+        for (int lb = 0; lb < Lx; lb += QB) {
+            const int nl = min(QB, Lx - lb);
+            double* sum = nsm + NOD_WARPS * 4 * nl * TILE;   // [4 nl][32]
+            double G[4][QB];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int l = 0; l < QB; ++l) G[a][l] = 0.0;
-        for (int m = wid; m < M; m += NOD_WARPS) {
-            const double q = short_rule ? I.xq8[m] : I.xq[m];
-            const double Wm = short_rule ? I.xw8[m] : I.xw[m];
-            double x, E, y;
-            if (full) {
-                y = sT * q;
-                x = uu + y;
-                E = Wm;
-            } else {
-                const double z = fma(q, v, -0.5 * v * v);
-                double ez;
-                if (short_rule) {
-                    ez = 1.0;
-#pragma unroll
-                    for (int j = 12; j >= 1; --j) ez = fma(ez * z, c_inv[j], 1.0);
+                for (int l = 0; l < QB; ++l) G[a][l] = 0.0;
+            for (int m = wid; m < M; m += NOD_WARPS) {
+                const double q = short_rule ? I.xq8[m] : I.xq[m];
+                const double Wm = short_rule ? I.xw8[m] : I.xw[m];
+                double x, E, y;
+                if (full) {
+                    y = sT * q;
+                    x = uu + y;
+                    E = Wm;
                 } else {
-                    ez = exp(z);
-                }
-                x = sT * q;
-                E = Wm * ez;
-                y = x - uu;
-            }
-            const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
-            double hm = 0.0, h = I.x_h0;
+                    const double z = fma(q, v, -0.5 * v * v);
+                    double ez;
+                    if (short_rule) {
+                        ez = 1.0;
 #pragma unroll
-            for (int l = 0; l < QB; ++l) {
-                if (l < Lx) {
-                    G[0][l] = fma(E, h, G[0][l]);
-                    G[1][l] = fma(e1, h, G[1][l]);
-                    G[2][l] = fma(e2, h, G[2][l]);
-                    G[3][l] = fma(e3, h, G[3][l]);
+                        for (int j = 12; j >= 1; --j) ez = fma(ez * z, c_inv[j], 1.0);
+                    } else {
+                        ez = exp(z);
+                    }
+                    x = sT * q;
+                    E = Wm * ez;
+                    y = x - uu;
+                }
+                const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+                double hm = 0.0, h = I.x_h0;
+                for (int l = 0; l < lb; ++l) {
                     const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
                     hm = h;
                     h = hn;
                 }
+#pragma unroll
+                for (int j = 0; j < QB; ++j) {
+                    if (j < nl) {
+                        const int l = lb + j;
+                        G[0][j] = fma(E, h, G[0][j]);
+                        G[1][j] = fma(e1, h, G[1][j]);
+                        G[2][j] = fma(e2, h, G[2][j]);
+                        G[3][j] = fma(e3, h, G[3][j]);
+                        const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
+                        hm = h;
+                        h = hn;
+                    }
+                }
             }
-        }
-        double* part = nsm;                                  // [NOD_WARPS][4 Lx][32]
-        double* sum = nsm + NOD_WARPS * 4 * Lx * TILE;       // [4 Lx][32]
+            if (lb > 0) __syncthreads();          // the previous block's readers of part and sum are done
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int l = 0; l < QB; ++l)
-                if (l < Lx) part[((wid * 4 + a) * Lx + l) * TILE + lane] = G[a][l];
-        __syncthreads();
-        for (int r = wid; r < 4 * Lx; r += NOD_WARPS) {
-            double s = 0.0;
-            for (int q = 0; q < NOD_WARPS; ++q) s += part[(q * 4 * Lx + r) * TILE + lane];
-            sum[r * TILE + lane] = s;
-        }
-        __syncthreads();
-        for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
-            const int a = o / Q, k = o - a * Q;
-            double s = 0.0;
-            for (int l = 0; l < Lx; ++l) s = fma(I.xH[l * Q + k], sum[(a * Lx + l) * TILE + lane], s);
-            if (role && (a & 1)) s = -s;
-            if (valid) {
+                for (int j = 0; j < QB; ++j)
+                    if (j < nl) part[((wid * 4 + a) * nl + j) * TILE + lane] = G[a][j];
+            __syncthreads();
+            for (int r = wid; r < 4 * nl; r += NOD_WARPS) {
+                double s = 0.0;
+                for (int q = 0; q < NOD_WARPS; ++q) s += part[(q * 4 * nl + r) * TILE + lane];
+                sum[r * TILE + lane] = s;
+            }
+            __syncthreads();
+            const bool last = lb + nl == Lx;
+            for (int o = wid; o < 4 * Q; o += NOD_WARPS) {
+                const int a = o / Q, k = o - a * Q;
                 const size_t r = (size_t)(a * 2 * Q + role * Q + k) * ld + i;
-                if (fp32) I.tab32[r] = (float)s;
-                else I.tab[r] = s;
+                double s = (lb > 0 && valid) ? I.tab[r] : 0.0;
+                for (int j = 0; j < nl; ++j) s = fma(I.xH[(lb + j) * Q + k], sum[(a * nl + j) * TILE + lane], s);
+                if (last && role && (a & 1)) s = -s;
+                if (valid) {
+                    if (last && fp32) I.tab32[r] = (float)s;
+                    else I.tab[r] = s;
+                }
             }
         }
         return;
@@ -1598,12 +1645,16 @@ __device__ bool stage_rows(const Inst& I, int i0, int k0, int nrows, int stage, 
 template <typename S, typename C, bool BULK>
 __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, unsigned char* smem_raw, int lane, int wy) {
     C* stab = reinterpret_cast<C*>(smem_raw);
-    void* tws = smem_raw + upd_table_bytes(I.ntab, sizeof(C));
-    S* Sw = reinterpret_cast<S*>(smem_raw + upd_stage_offset(I.ntab, sizeof(C)));
+    void* tws = smem_raw + upd_table_bytes(I.trows, sizeof(C));
+    S* Sw = reinterpret_cast<S*>(smem_raw + upd_stage_offset(I.trows, sizeof(C)));
     double* ex = reinterpret_cast<double*>(Sw);                 // after the rows are consumed
-    S* fo = reinterpret_cast<S*>(smem_raw + upd_fo_offset(I.ntab, I.ukc, sizeof(C), sizeof(S)));
+    S* fo = reinterpret_cast<S*>(smem_raw + upd_fo_offset(I.trows, I.ukc, sizeof(C), sizeof(S)));
     const int i = i0 + lane;
-    const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, ntab = I.ntab;
+    const int N = I.N, ld = I.ld, Q = I.Q, Tc = I.Tc, trows = I.trows;
+    // compact table: the x-projection rows of the NKX x-velocities from kx0 on (the chunk's),
+    // then the 4 Tc transverse rows and 1/tau; NKX = 2Q (kx0 = 0) is the whole table
+    const int NKX = (trows - 4 * Tc - 1) / 4;
+    const int kx0 = NKX == 2 * Q ? 0 : k0 / Tc;
     const bool valid = i < N;
     const C* tabc = Tabs<C>::tab(I);
     const C* pxc = Tabs<C>::px(I);
@@ -1614,17 +1665,24 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     if (!stage_rows<S, BULK>(I, i0, k0, k1 - k0, stage, Sw, fo, lane, wy)) return false;
     // rows in batches: all loads of a batch are issued before its shared-memory stores
     constexpr int TB = 16;
-    for (int r0 = wy; r0 < ntab; r0 += UPD_WARPS * TB) {
+    for (int r0 = wy; r0 < trows; r0 += UPD_WARPS * TB) {
         C tmp[TB];
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int r = r0 + b * UPD_WARPS;
-            tmp[b] = (valid && r < ntab) ? tabc[(size_t)r * ld + i] : (C)0;
+            int gr = -1;                              // row of the instance's table
+            if (r < 4 * NKX) {
+                const int a = r / NKX, kx = kx0 + (r - a * NKX);
+                if (kx < 2 * Q) gr = a * 2 * Q + kx;
+            } else if (r < trows) {
+                gr = 8 * Q + (r - 4 * NKX);
+            }
+            tmp[b] = (valid && gr >= 0) ? tabc[(size_t)gr * ld + i] : (C)0;
         }
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int r = r0 + b * UPD_WARPS;
-            if (r < ntab) stab[r * TILE + lane] = tmp[b];
+            if (r < trows) stab[r * TILE + lane] = tmp[b];
         }
     }
     load_tw<S>(I, tws, wy * TILE + lane, UPD_WARPS * TILE);
@@ -1637,7 +1695,7 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const uint32_t seed = sizeof(S) == 4 ? sr_seed(I, stage) : 0u;
     const C nwL = (C)I.misc[M_NWL], nwR = (C)I.misc[M_NWR];
     const C xpi = valid ? Tabs<C>::xpinv(I)[i] : (C)0;
-    const C invtau = stab[(8 * Q + 4 * Tc) * TILE + lane];
+    const C invtau = stab[(4 * NKX + 4 * Tc) * TILE + lane];
     const bool force = I.accel_y != 0.0 && I.form != FORM_REDUCED1D;
     const int Tz = I.form == FORM_UNREDUCED ? I.Qz : 2;
     const C ay = (C)I.accel_y;
@@ -1698,7 +1756,7 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
             }
             C tgt = 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) tgt += stab[(a * 2 * Q + kx) * TILE + lane] * stab[(8 * Q + a * Tc + t) * TILE + lane];
+            for (int a = 0; a < 4; ++a) tgt += stab[(a * NKX + kx - kx0) * TILE + lane] * stab[(4 * NKX + a * Tc + t) * TILE + lane];
             const C fi = v[3];
             const C Fk = stage == 1 ? (C)0 : (C)*fk;
             L += (tgt - fi) * invtau;
@@ -1741,7 +1799,7 @@ __global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restr
     if (*I.status != FDLB_ACTIVE || I.smem_res) return;
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
     if (!update_item<S, C, true>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y)) return;
-    if (I.mgroups > 1) chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_stage_offset(I.ntab, sizeof(C))) + UPD_WARPS * MOM_SUMS * TILE);
+    if (I.mgroups > 1) chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_stage_offset(I.trows, sizeof(C))) + UPD_WARPS * MOM_SUMS * TILE);
 }
 
 // Moments of buffer `buf` from scratch (creation, new profiles, a loaded state): one block per

@@ -46,7 +46,7 @@ def test_abi_version_and_struct(F):
 def test_parameter_validation(F):
     ok = F.Params(nx=50, qx_half=4, qy=4, qz=4, kn=0.1, eta0=0.1)
     assert F.workspace_bytes([ok]) > 0
-    bad = [dict(nx=4), dict(qx_half=0), dict(qx_half=17), dict(qy=1), dict(qz=2), dict(qy=0, qz=4),
+    bad = [dict(nx=4), dict(qx_half=0), dict(qx_half=33), dict(qy=1), dict(qz=2), dict(qy=0, qz=4),
            dict(eta0=0.5), dict(kn=0.0), dict(T_left=0.0), dict(qy=0, qz=0, U_left=0.1)]
     for kw in bad:
         p = F.Params(**{**ok.__dict__, **kw})
@@ -85,14 +85,18 @@ def test_null_context_calls_fail_cleanly(F):
 
 
 def test_x_quadrature_validation(F):
-    """The full-range x rule has order 2 qx_half <= 16; its tables hold 2 qx_half polynomials."""
+    """Orders: half-range up to 32 per side (Table 1 of Sec. IV reaches 29), full-range up to 200
+    (App. A's comparison needs ~200); the full rule's tables hold 2 qx_half polynomials."""
     base = dict(nx=64, qx_half=8, qy=4, qz=0, kn=0.1, eta0=0.1)
     b_half = F.workspace_bytes([F.Params(**base)])
     b_full = F.workspace_bytes([F.Params(**base, x_quadrature="full")])
     assert b_full > b_half                      # w_k h_l(p_k) for l < 16 instead of l < 8
+    assert F.workspace_bytes([F.Params(**{**base, "qx_half": 100}, x_quadrature="full")]) > 0
     with pytest.raises(F.FdlbError):
-        F.workspace_bytes([F.Params(**{**base, "qx_half": 9}, x_quadrature="full")])
-    assert F.workspace_bytes([F.Params(**{**base, "qx_half": 9})]) > 0
+        F.workspace_bytes([F.Params(**{**base, "qx_half": 101}, x_quadrature="full")])
+    assert F.workspace_bytes([F.Params(**{**base, "qx_half": 32})]) > 0
+    with pytest.raises(F.FdlbError):
+        F.workspace_bytes([F.Params(**{**base, "qx_half": 33})])
     lib = F.load()
     c = F.Params(**base).to_c()
     c.x_quadrature = 2

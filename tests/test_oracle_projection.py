@@ -114,3 +114,39 @@ def test_force_kernel(Q):
     for u, T in ((0.2, 1.1), (-0.5, 0.8)):
         P = qd.project_full(r.nodes, u, T)
         np.testing.assert_allclose(K @ P[0], -P[1] / T, atol=1e-14)
+
+
+@pytest.mark.parametrize("Q", [20, 29])
+@pytest.mark.parametrize("u,T", [(0.0, 1.0), (0.05, 0.95), (-0.3, 1.1)])
+def test_half_projection_high_orders(Q, u, T):
+    """The orders of Table 1 (Sec. IV, up to 29 per side): moment exactness s <= Q - 1, relative
+    to the sum of the magnitudes of the terms (the high powers of the nodes are large)."""
+    p = qd.half_range_rule(Q).nodes
+    P = qd.project_half(p, u, T)
+    for a in range(4):
+        want = half_line_moments(u, T, Q - 1, a)
+        for s in range(Q):
+            got = float(np.sum(P[a] * p ** s))
+            scale = float(np.sum(np.abs(P[a]) * p ** s))
+            assert abs(got - want[s]) <= 1e-12 * max(scale, 1.0), (a, s, got, want[s])
+
+
+@pytest.mark.parametrize("Q", [20, 29])
+def test_half_projection_high_orders_reference_state(Q):
+    r = qd.half_range_rule(Q)
+    np.testing.assert_allclose(qd.project_half(r.nodes, 0.0, 1.0)[0], r.weights, rtol=1e-11, atol=1e-18)
+
+
+@pytest.mark.parametrize("Q", [24, 40])
+def test_full_projection_high_orders(Q):
+    """Full-range orders beyond 16 (App. A): weights at rest, moment exactness s <= Q - 1."""
+    r = qd.full_range_rule(Q)
+    np.testing.assert_allclose(qd.project_full(r.nodes, 0.0, 1.0)[0], r.weights, rtol=1e-10, atol=1e-20)
+    u, T = 0.3, 1.05
+    P = qd.project_full(r.nodes, u, T)
+    for a in range(4):
+        want = full_line_moments(u, T, Q - 1, a)
+        for s in range(Q):
+            got = float(np.sum(P[a] * r.nodes ** s))
+            scale = float(np.sum(np.abs(P[a]) * np.abs(r.nodes) ** s))
+            assert abs(got - want[s]) <= 1e-12 * max(scale, 1.0), (a, s)
