@@ -536,8 +536,11 @@ __device__ void moments_final_tile(const Inst& I, int i0, double* ss, int tid, i
 constexpr int CL_ROWS = 5 + 8 + 15;    // closure item: gradients, scalars, coefficients
 
 __host__ __device__ inline int nodal_smem_doubles(int qmax) {
-    if (qmax > QMAX) qmax = QMAX;                // larger x orders run in blocks of QMAX polynomials
-    const int r01 = (NOD_WARPS + 1) * 4 * qmax * TILE;
+    // larger x orders run in blocks of QMAX polynomials, with the recurrence state of every
+    // auxiliary point kept between blocks: [M][2][32] more (M bounded for either x rule)
+    const int mst = qmax > QMAX ? (aux_points_half(qmax) > qmax / 2 + 2 ? aux_points_half(qmax) : qmax / 2 + 2) : 0;
+    if (qmax > QMAX) qmax = QMAX;
+    const int r01 = (NOD_WARPS + 1) * 4 * qmax * TILE + 2 * mst * TILE;
     const int r2 = (CL_ROWS + 4 * QYMAX + 3 * QZMAX + 8 * QYMAX + 2 * MYMAX * (QYMAX + 1)) * TILE;
     return r01 > r2 ? r01 : r2;
 }
@@ -600,6 +603,7 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
     const df sT = df_of(xs[0][lane]), uu = df_of(xs[1][lane]), v = df_of(xs[2][lane]), hv2 = df_of(xs[3][lane]);
     const df one = {1.0f, 0.0f};
     float2* part = reinterpret_cast<float2*>(nsm);                  // [NOD_WARPS][4 nl][32]
+    float2* hst = part + (NOD_WARPS + 1) * 4 * QB * TILE;           // [M][2][32] recurrence state (Lx > QB)
     // blocks of QB polynomials as in the FP64 branch; the chain of H products continues across
     // blocks as float pairs in the instance's FP64 table rows (8 bytes each), and the last
     // block rounds it into the FP32 table
@@ -636,10 +640,9 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
             }
             const df e1 = E * y, e2 = e1 * y, e3 = e2 * y;
             df hm = {0.0f, 0.0f}, h = df_of(I.x_h02);
-            for (int l = 0; l < lb; ++l) {
-                const df hn = ((x - df_of(I.xa2[l])) * h - df_of(I.xb2[l]) * hm) * df_of(I.xib2[l + 1]);
-                hm = h;
-                h = hn;
+            if (lb > 0) {
+                hm = df_of(hst[(2 * m) * TILE + lane]);
+                h = df_of(hst[(2 * m + 1) * TILE + lane]);
             }
 #pragma unroll
             for (int j = 0; j < QB; ++j) {
@@ -653,6 +656,10 @@ __device__ void xproj_df(const Inst& I, int i0, int role, double* nsm) {
                     hm = h;
                     h = hn;
                 }
+            }
+            if (lb + nl < Lx) {
+                hst[(2 * m) * TILE + lane] = make_float2(hm.hi, hm.lo);
+                hst[(2 * m + 1) * TILE + lane] = make_float2(h.hi, h.lo);
             }
         }
         if (lb > 0) __syncthreads();              // the previous block's readers of part and sum are done
@@ -999,9 +1006,11 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
         const bool short_rule = !full && use_short == 1 && Q <= 12;
         const int M = full ? I.Mx : (short_rule ? MX8 : I.Mx);
         double* part = nsm;                                  // [NOD_WARPS][4 nl][32]
+        double* hst = nsm + (NOD_WARPS + 1) * 4 * QB * TILE; // [M][2][32] recurrence state (Lx > QB)
         // the polynomials in blocks of QB: per block the sums over the auxiliary points (the
-        // recurrence run from l = 0 again), then the H products, whose chain continues across
-        // blocks in the instance's FP64 table rows (signed and written at the last block)
+        // recurrence continued from the previous block's state), then the H products, whose
+        // chain continues across blocks in the instance's FP64 table rows (signed and written at
+        // the last block)
         for (int lb = 0; lb < Lx; lb += QB) {
             const int nl = min(QB, Lx - lb);
             double* sum = nsm + NOD_WARPS * 4 * nl * TILE;   // [4 nl][32]
@@ -1033,11 +1042,12 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
                     y = x - uu;
                 }
                 const double e1 = E * y, e2 = e1 * y, e3 = e2 * y;
+                // recurrence state at the block's first polynomial: from the start, or as the
+                // previous block left it (this thread stored it)
                 double hm = 0.0, h = I.x_h0;
-                for (int l = 0; l < lb; ++l) {
-                    const double hn = ((x - I.xa[l]) * h - I.xb[l] * hm) * I.xib[l + 1];
-                    hm = h;
-                    h = hn;
+                if (lb > 0) {
+                    hm = hst[(2 * m) * TILE + lane];
+                    h = hst[(2 * m + 1) * TILE + lane];
                 }
 #pragma unroll
                 for (int j = 0; j < QB; ++j) {
@@ -1051,6 +1061,10 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
                         hm = h;
                         h = hn;
                     }
+                }
+                if (lb + nl < Lx) {
+                    hst[(2 * m) * TILE + lane] = hm;
+                    hst[(2 * m + 1) * TILE + lane] = h;
                 }
             }
             if (lb > 0) __syncthreads();          // the previous block's readers of part and sum are done

@@ -1,0 +1,143 @@
+"""Velocity-quadrature studies of Sec. IV and App. A in the paper's geometry.
+
+  python -m paper_2308_15407_gb300.quadrature_study [table1|fullhalf|heatflux] [--cells-per-sigma 20]
+
+table1    The convergence test behind the paper's Table 1: for each flow (Fourier with
+          Delta T = 0.1, Couette with U_w = 1, Poiseuille with a_y = 0.001 in v^2/sigma),
+          confinement R in {4, 10} and reduced density eta0 in {0.01, 0.1, 0.2}, the error
+          eps = max |M - M_ref| / (max M_ref - min M_ref) (M = T, u_y, u_y) of half-range orders
+          4 .. 29 per side against a reference, and the smallest order with eps < 1 %.  The
+          paper's reference is order 200 and its spacing sigma/100; here the reference is the
+          library's largest half-range order, 32 per side, and the spacing is an argument.
+fullhalf  App. A's comparison (R = 10, eta0 = 0.01): full-range orders 16 .. 200 against the
+          same reference, beside half-range orders.
+heatflux  Fourier flow (Delta T = 0.1): the heat flux q_x / n0 across the channel against the
+          Knudsen number (varied through R at fixed eta0) for eta0 in {0.01, 0.1, 0.2}.
+
+Steady states in FP64 to per-step residual 1e-9 under a wall-clock cap; RET-FM contact value
+(the paper's); Q_y = 5 for the 2D flows.  Everything runs through the public binding; the
+output is one JSON document.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+FLOWS = [("fourier", dict(dT=0.1), "T"), ("couette", dict(U_w=1.0), "uy"), ("poiseuille", dict(a_y=0.001), "uy")]
+HALF_ORDERS = (4, 6, 8, 11, 15, 20, 24, 29)
+REF_ORDER = 32
+TOL = 1e-9
+
+
+def _steady(F, dicts, cap_s):
+    import torch
+    s = F.Solver([F.Params(**d) for d in dicts])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        s.run(TOL, 5_000_000, check_every=2000, timeout_s=cap_s)
+    except F.FdlbError:
+        pass
+    torch.cuda.synchronize()
+    return s, time.perf_counter() - t0
+
+
+def _eps(M, R):
+    return float(np.max(np.abs(M - R)) / (R.max() - R.min()))
+
+
+def table1(cells_per_sigma=20, cap_s=900.0):
+    from . import fdlb as F
+    from . import workloads as W
+    cases, dicts = [], []
+    for fl, kw, key in FLOWS:
+        for R in (4, 10):
+            for eta in (0.01, 0.1, 0.2):
+                for q in (REF_ORDER,) + HALF_ORDERS:
+                    dicts.append(W.paper_geometry(R, eta, qx_half=q, cells_per_sigma=cells_per_sigma, flow=fl, **kw))
+                cases.append((fl, key, R, eta))
+    s, sec = _steady(F, dicts, cap_s)
+    _, st, steps = s.status()
+    out = {"cells_per_sigma": cells_per_sigma, "reference_order": REF_ORDER, "seconds": sec, "tolerance": TOL,
+           "all_converged": bool(np.all(st == F.CONVERGED)), "cases": []}
+    n = 1 + len(HALF_ORDERS)
+    for c, (fl, key, R, eta) in enumerate(cases):
+        base = c * n
+        ref = s.moments(base)[key]
+        eps = {q: _eps(s.moments(base + 1 + j)[key], ref) for j, q in enumerate(HALF_ORDERS)}
+        conv = [bool(st[base + j] == F.CONVERGED) for j in range(n)]
+        first = next((q for q in HALF_ORDERS if eps[q] < 0.01), None)
+        out["cases"].append({"flow": fl, "R": R, "eta0": eta, "eps": eps, "smallest_order_below_1pct": first,
+                             "converged": all(conv), "steps_reference": int(steps[base])})
+    return out
+
+
+def fullhalf(cells_per_sigma=20, cap_s=900.0, full_orders=(16, 32, 64, 100, 200), half_orders=(8, 16, 29)):
+    from . import fdlb as F
+    from . import workloads as W
+    dicts = []
+    for fl, kw, key in FLOWS:
+        dicts.append(W.paper_geometry(10, 0.01, qx_half=REF_ORDER, cells_per_sigma=cells_per_sigma, flow=fl, **kw))
+        for q in half_orders:
+            dicts.append(W.paper_geometry(10, 0.01, qx_half=q, cells_per_sigma=cells_per_sigma, flow=fl, **kw))
+        for o in full_orders:
+            dicts.append(W.paper_geometry(10, 0.01, qx_half=o // 2, cells_per_sigma=cells_per_sigma, flow=fl,
+                                          x_quadrature="full", **kw))
+    s, sec = _steady(F, dicts, cap_s)
+    _, st, steps = s.status()
+    n = 1 + len(half_orders) + len(full_orders)
+    out = {"cells_per_sigma": cells_per_sigma, "reference": f"half-range {REF_ORDER} per side", "seconds": sec,
+           "all_converged": bool(np.all(st == F.CONVERGED)), "flows": []}
+    for fi, (fl, _, key) in enumerate(FLOWS):
+        base = fi * n
+        ref = s.moments(base)[key]
+        half = {q: _eps(s.moments(base + 1 + j)[key], ref) for j, q in enumerate(half_orders)}
+        full = {o: _eps(s.moments(base + 1 + len(half_orders) + j)[key], ref) for j, o in enumerate(full_orders)}
+        row = {"flow": fl, "half_eps": half, "full_eps": full,
+               "converged": [bool(x == F.CONVERGED) for x in st[base:base + n]]}
+        if fl == "poiseuille":
+            mfr = lambda i: float(np.mean(s.moments(i)["n"] * s.moments(i)["uy"]))
+            row["mean_n_uy"] = {"reference": mfr(base),
+                                "full": {o: mfr(base + 1 + len(half_orders) + j) for j, o in enumerate(full_orders)}}
+        out["flows"].append(row)
+    return out
+
+
+def heatflux(cells_per_sigma=20, cap_s=600.0, R_values=(2, 3, 4, 6, 10, 20), qx_half=11):
+    from . import fdlb as F
+    from . import workloads as W
+    dicts, tags = [], []
+    for eta in (0.01, 0.1, 0.2):
+        for R in R_values:
+            d = W.paper_geometry(R, eta, qx_half=qx_half, cells_per_sigma=max(cells_per_sigma, int(np.ceil(60 / (R - 1)))),
+                                 flow="fourier", dT=0.1)
+            dicts.append(d)
+            chi0 = (2.0 - eta) / (2.0 * (1.0 - eta) ** 3)
+            tags.append({"eta0": eta, "R": R, "Kn_L": 1.0 / (6.0 * np.sqrt(2.0) * eta * chi0 * R)})
+    s, sec = _steady(F, dicts, cap_s)
+    _, st, _ = s.status()
+    rows = []
+    for i, t in enumerate(tags):
+        M = s.moments(i)
+        # q_x is uniform at steady state (up to truncation); report its channel mean and spread.
+        # Channel-width units: q_x in n0 (k_B T0/m)^(3/2), the paper's q_x / n0.
+        rows.append({**t, "qx_over_n0": float(np.mean(M["qx"])), "qx_spread": float(np.ptp(M["qx"])),
+                     "converged": bool(st[i] == F.CONVERGED)})
+    return {"cells_per_sigma": cells_per_sigma, "qx_half": qx_half, "seconds": sec, "rows": rows}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["table1", "fullhalf", "heatflux"])
+    ap.add_argument("--cells-per-sigma", type=int, default=20)
+    ap.add_argument("--cap-s", type=float, default=900.0)
+    a = ap.parse_args()
+    fn = {"table1": table1, "fullhalf": fullhalf, "heatflux": heatflux}[a.what]
+    print(json.dumps(fn(a.cells_per_sigma, a.cap_s)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
