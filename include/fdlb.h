@@ -103,7 +103,7 @@ extern "C" {
  *                 variant the paper compares against; its nodes are +-p_k (no zero node), so
  *                 the 2 qx_half x-velocities keep their layout.  The discrete equilibrium is
  *                 the expansion over the whole axis truncated at order 2 qx_half - 1.  Needs
- *                 qx_half <= 8.  Walls, fluxes and moments are the same as with FDLB_XQ_HALF. */
+ *                 qx_half <= 100.  Walls, fluxes and moments are the same as with FDLB_XQ_HALF. */
 #define FDLB_XQ_HALF     0
 #define FDLB_XQ_FULL     1
 
@@ -124,8 +124,8 @@ typedef struct fdlb_params {
     int32_t  flow;        /* FDLB_FOURIER | FDLB_COUETTE | FDLB_POISEUILLE */
     int32_t  nx;          /* grid nodes, 8 <= nx <= 4096 */
     int32_t  grid;        /* FDLB_GRID_UNIFORM | FDLB_GRID_TANH */
-    int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..16 (2*qx_half x-velocities);
-                             with FDLB_XQ_FULL half the full-range order, 1..8 */
+    int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..32 (2*qx_half x-velocities);
+                             with FDLB_XQ_FULL half the full-range order, 1..100 (order <= 200) */
     int32_t  qy;          /* full-range order on y, 0 or 2..8; 0 = 1D reduced (p_y integrated out) */
     int32_t  qz;          /* full-range order on z, 0 or 3..8; 0 = (phi, theta) reduced slots */
     int32_t  precision;   /* FDLB_FP64 | FDLB_FP32_STORAGE | FDLB_FP32_THEN_FP64 */
@@ -277,7 +277,7 @@ int fdlb_profile(fdlb_ctx* ctx, int32_t on);
 int fdlb_profile_read(fdlb_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 
 /* Largest scratch fdlb_step_noalloc can use (8 MiB = 8,388,608 B): enough for one instance
- * of nx = 400 with 16 x-velocities (qx_half = 8) x 6 x 6 in FP64 (8,218,624 B, the
+ * of nx = 400 with 16 x-velocities (qx_half = 8) x 6 x 6 in FP64 (8,218,880 B, the
  * Poiseuille set-up of Sec. IV), or the 200-node Couette instance with 12 x 6 x 4 velocities
  * (1.7 MB in FP32 storage).  fdlb_workspace_bytes(params, 1) is the amount an instance needs;
  * nx = 400 with qx_half = 16 x 6 x 6 (15.9 MB in FP64) is rejected. */
