@@ -56,7 +56,7 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2308_15407_gb300", "csrc", "fdlb_kernels.
 # ncu DRAM bytes (read + write) per k_update<float,float> launch on the 12-instance sweep,
 # cold cache, mean over the three stages of one capture, with the SHA-256 prefix of the
 # kernel source it was taken on; the bench reports it only while the source is unchanged.
-UPDATE_TRAFFIC = {"bytes": 6688512, "kernel_src_sha16": "62dc3d5a49511539"}
+UPDATE_TRAFFIC = {"bytes": 6691499, "kernel_src_sha16": "37dfbdfebdbecda5"}
 
 
 def kernel_src_sha16():
