@@ -124,7 +124,7 @@ typedef struct fdlb_params {
     int32_t  flow;        /* FDLB_FOURIER | FDLB_COUETTE | FDLB_POISEUILLE */
     int32_t  nx;          /* grid nodes, 8 <= nx <= 4096 */
     int32_t  grid;        /* FDLB_GRID_UNIFORM | FDLB_GRID_TANH */
-    int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..32 (2*qx_half x-velocities);
+    int32_t  qx_half;     /* half-range Gauss-Hermite order per side, 1..100 (2*qx_half x-velocities);
                              with FDLB_XQ_FULL half the full-range order, 1..100 (order <= 200) */
     int32_t  qy;          /* full-range order on y, 0 or 2..8; 0 = 1D reduced (p_y integrated out) */
     int32_t  qz;          /* full-range order on z, 0 or 3..8; 0 = (phi, theta) reduced slots */
@@ -339,7 +339,7 @@ int fdlb_mlp_train_step(fdlb_mlp* h, const float* dev_x, const float* dev_y, int
 /* Host-only: the library's own Gauss rules (for checking the tables; no GPU needed).
  * kind 0 = half-range Gauss-Hermite on [0, inf) (Sec. III A 2), kind 1 = full-range (App. A);
  * weights are normalised to the weight omega(p) = exp(-p^2/2)/sqrt(2 pi).  nodes/weights
- * receive q values.  Errors: FDLB_EINVAL. */
+ * receive q values; q in 1..100 (half-range) or 1..200 (full-range).  Errors: FDLB_EINVAL. */
 int fdlb_quadrature(int32_t kind, int32_t q, double* nodes, double* weights);
 
 #ifdef __cplusplus

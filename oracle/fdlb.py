@@ -243,11 +243,13 @@ def weno5_face(vm2, vm1, v0, vp1, vp2):
     # limiting case: weight only on the vanishing indicators
     wz = np.where(zero, delta, 0.0)
     wz = wz / np.where(anyzero, wz.sum(axis=0), 1.0)
-    # regular case: delta_q/phi_q^2, rescaled by phi_min^2
+    # regular case: delta_q/phi_q^2, rescaled by phi_min^2 (evaluated everywhere; where an
+    # indicator vanishes it may overflow, and the limiting case above is taken instead)
     pmin = np.where(anyzero, 1.0, phi.min(axis=0))
     safe = np.where(zero, 1.0, phi)
-    wr = delta * (pmin / safe) ** 2
-    wr = wr / wr.sum(axis=0)
+    with np.errstate(over="ignore", invalid="ignore"):
+        wr = delta * (pmin / safe) ** 2
+        wr = wr / wr.sum(axis=0)
     w = np.where(anyzero[None], wz, wr)
     return w[0] * F1 + w[1] * F2 + w[2] * F3
 

@@ -18,23 +18,30 @@ Sources in the paper:
     Lagrange basis polynomial of node k (Christoffel-Darboux).  That integral is
     what ``project_half`` / ``project_full`` evaluate.
 
-All rules are built from exact moments in 200-digit decimal arithmetic
-(Stieltjes procedure on the moment functional, Newton-polished roots,
-Christoffel weights) and only then rounded to float64.
+All rules are built from exact moments in decimal arithmetic of at least 200
+digits (Stieltjes procedure on the moment functional, Newton-polished roots,
+Christoffel weights) and only then rounded to float64.  The moment route loses
+digits with the order (the Hankel matrix of the moments is ill-conditioned), so
+orders above 46 work with 60 + 3 Q digits.
 """
 from __future__ import annotations
 
 import functools
 import math
-from decimal import Decimal, getcontext
+from decimal import Decimal, getcontext, localcontext
 
 import numpy as np
 
 _PREC = 200
+_prec_now = [_PREC]          # working precision of the rule being built
+
+
+def _rule_prec(Q: int) -> int:
+    return max(_PREC, 60 + 3 * Q)
 
 
 def _ctx():
-    getcontext().prec = _PREC
+    getcontext().prec = _prec_now[0]
 
 
 def _pi() -> Decimal:
@@ -45,7 +52,7 @@ def _pi() -> Decimal:
         x = Decimal(1) / n
         x2 = x * x
         term, total, k = x, x, 1
-        eps = Decimal(10) ** (-(_PREC + 5))
+        eps = Decimal(10) ** (-(_prec_now[0] + 5))
         while abs(term) > eps:
             term *= -x2
             total += term / (2 * k + 1)
@@ -87,7 +94,18 @@ class GaussRule:
     Christoffel weights (decimal and float64)."""
 
     def __init__(self, Q: int, moment):
+        prev = _prec_now[0]
+        _prec_now[0] = _rule_prec(Q)
+        try:
+            self._build(Q, moment)
+        finally:
+            _prec_now[0] = prev
+            _ctx()
+
+    def _build(self, Q: int, moment):
         _ctx()
+        prec = _prec_now[0]
+        self.prec = prec
         self.Q = Q
         mom = [moment(s) for s in range(2 * Q + 4)]
 
@@ -135,7 +153,7 @@ class GaussRule:
                 f, df = self._eval_monic_with_derivative(Q, x)
                 dx = f / df
                 x -= dx
-                if abs(dx) < Decimal(10) ** (-(_PREC - 20)):
+                if abs(dx) < Decimal(10) ** (-(prec - 20)):
                     break
             nodes.append(x)
         self.nodes_dec = nodes
@@ -155,11 +173,14 @@ class GaussRule:
         return p1, d1
 
     def eval_ortho(self, l: int, x: Decimal) -> Decimal:
-        """Orthonormal polynomial h_l at x (Horner on its decimal coefficients)."""
-        r = Decimal(0)
-        for c in reversed(self.ortho[l]):
-            r = r * x + c
-        return r
+        """Orthonormal polynomial h_l at x (Horner on its decimal coefficients, at the rule's
+        working precision)."""
+        with localcontext() as c:
+            c.prec = self.prec
+            r = Decimal(0)
+            for co in reversed(self.ortho[l]):
+                r = r * x + co
+            return +r
 
 
 @functools.lru_cache(maxsize=None)
@@ -188,8 +209,10 @@ def lagrange_basis(nodes: np.ndarray, x: np.ndarray) -> np.ndarray:
 # Order of the auxiliary rules used to evaluate the projection integrals.
 # Full line: the integrand is polynomial x Gaussian after the change of variable,
 # so the auxiliary Gauss-Hermite rule is exact once 2M > degree.  Half line: the
-# integrand is polynomial x omega(q) x exp(q v - v^2/2); a 40-point rule leaves a
-# truncation error far below float64 round-off for |v| <= 1.
+# integrand is polynomial x omega(q) x exp(q v - v^2/2); with 2M >= Q + 60 (Q the
+# order projected on) the rule integrates the polynomial of degree Q + 2 times the
+# exponential's Taylor series far past the float64 round-off for |v| <= 1/2: 40
+# points up to Q = 20, Q/2 + 30 above.
 AUX_HALF = 40
 AUX_FULL = 24
 
@@ -201,14 +224,14 @@ def project_half(nodes: np.ndarray, u, T, amax: int = 3) -> np.ndarray:
     Maxwellian.  value[a, k, ...] = int_0^inf l_k(p) (p-u)^a g(p; u, T) dp,
     which is the truncated half-range expansion (Sec. III A 2, Eq. (hh_gk)).
     Evaluated with p = sqrt(T) q, which turns g sqrt(T) dq into
-    omega(q) exp(q v - v^2/2) dq with v = u/sqrt(T), and an AUX_HALF-point
-    half-range Gauss rule in q.  u, T broadcast (arrays over grid nodes).
+    omega(q) exp(q v - v^2/2) dq with v = u/sqrt(T), and a half-range Gauss rule
+    in q of max(AUX_HALF, Q/2 + 30) points.  u, T broadcast (arrays over grid nodes).
 
     The negative half-axis value at node -p_k is (-1)^a project_half(nodes, -u, T)[a, k]
     (substitute p -> -p)."""
     u = np.asarray(u, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
-    aux = half_range_rule(AUX_HALF)
+    aux = half_range_rule(max(AUX_HALF, len(nodes) // 2 + 30))
     q = aux.nodes.reshape((-1,) + (1,) * u.ndim)
     W = aux.weights.reshape((-1,) + (1,) * u.ndim)
     v = u / np.sqrt(T)

@@ -167,13 +167,15 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 
 // Monic recurrence pi_{l+1} = (p - alpha_l) pi_l - beta_l pi_{l-1}, l = 0..L-1, for the
 // half-range weight omega(p) = exp(-p^2/2)/sqrt(2 pi) on [0, inf), by the Stieltjes
-// procedure on the discrete measure of a composite Gauss-Legendre rule on [0, 20]
-// (the weight below 1e-86 beyond); beta_0 = mass = 1/2.
+// procedure on the discrete measure of a composite Gauss-Legendre rule on [0, 32] (panels
+// of width 1/4; the weight is below 1e-222 beyond, where the polynomials of the orders up to
+// 101 have long passed their largest zero, ~22.3 at order 101); beta_0 = mass = 1/2.  The
+// monic values stay below 32^101 and their squares times the weight in range.
 void half_range_recurrence(int L, std::vector<double>& alpha, std::vector<double>& beta) {
     std::vector<double> gx, gw;
-    const int npt = 24, panels = 80;
+    const int npt = 24, panels = 128;
     gauss_legendre(npt, gx, gw);
-    const double hi = 20.0, h = hi / panels;
+    const double hi = 32.0, h = hi / panels;
     std::vector<double> t, W;
     for (int pnl = 0; pnl < panels; ++pnl)
         for (int j = 0; j < npt; ++j) {
@@ -186,12 +188,22 @@ void half_range_recurrence(int L, std::vector<double>& alpha, std::vector<double
     alpha.assign(L, 0.0);
     beta.assign(L, 0.0);
     double norm_prev = 1.0;
+    // the inner products summed with Neumaier's compensated summation (the terms span many
+    // orders of magnitude at high degree)
+    auto csum = [](double& s, double& c, double v) {
+        const double t2 = s + v;
+        c += std::fabs(s) >= std::fabs(v) ? (s - t2) + v : (v - t2) + s;
+        s = t2;
+    };
     for (int l = 0; l < L; ++l) {
-        double nrm = 0, xn = 0;
+        double nrm = 0, xn = 0, cn = 0, cx = 0;
         for (size_t j = 0; j < P; ++j) {
-            nrm += W[j] * pc[j] * pc[j];
-            xn += W[j] * t[j] * pc[j] * pc[j];
+            const double q = W[j] * pc[j] * pc[j];
+            csum(nrm, cn, q);
+            csum(xn, cx, q * t[j]);
         }
+        nrm += cn;
+        xn += cx;
         alpha[l] = (double)(xn / nrm);
         beta[l] = (double)(l == 0 ? nrm : nrm / norm_prev);
         for (size_t j = 0; j < P; ++j) pn[j] = (t[j] - (double)alpha[l]) * pc[j] - (double)beta[l] * pm[j];
@@ -328,7 +340,7 @@ int validate(const fdlb_params& p, std::string& why) {
     if (p.struct_size != sizeof(fdlb_params)) return bad("struct_size != sizeof(fdlb_params)");
     if (p.nx < 8 || p.nx > 4096) return bad("nx must be in [8, 4096]");
     if (p.qx_half < 1) return bad("qx_half must be >= 1");
-    if (p.x_quadrature == FDLB_XQ_HALF && p.qx_half > QX_HALF_MAX) return bad("qx_half must be in [1, 32] (half-range x)");
+    if (p.x_quadrature == FDLB_XQ_HALF && p.qx_half > QX_HALF_MAX) return bad("qx_half must be in [1, 100] (half-range x)");
     if (p.qy != 0 && (p.qy < 2 || p.qy > QYMAX)) return bad("qy must be 0 or in [2, 8]");
     if (p.qz != 0 && (p.qz < 3 || p.qz > QZMAX)) return bad("qz must be 0 or in [3, 8]");
     if (p.qy == 0 && p.qz != 0) return bad("qy == 0 (1D reduced) requires qz == 0");
@@ -515,7 +527,8 @@ void count_work(const std::vector<fdlb_params>& p, int& n_upd, int& n_nod) {
 }  // namespace
 
 extern "C" int fdlb_quadrature(int32_t kind, int32_t q, double* nodes, double* weights) {
-    if ((kind != 0 && kind != 1) || q < 1 || q > 64 || !nodes || !weights) return fail(nullptr, FDLB_EINVAL, "fdlb_quadrature: bad arguments");
+    if ((kind != 0 && kind != 1) || q < 1 || q > (kind == 0 ? QX_HALF_MAX : LXMAX) || !nodes || !weights)
+        return fail(nullptr, FDLB_EINVAL, "fdlb_quadrature: bad arguments");
     Rule r = make_rule(kind, q);
     for (int k = 0; k < q; ++k) { nodes[k] = r.x[k]; weights[k] = r.w[k]; }
     return FDLB_OK;

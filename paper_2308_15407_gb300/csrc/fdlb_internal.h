@@ -8,7 +8,7 @@
 namespace fdlb {
 
 constexpr int QMAX = 16;        // x polynomials per block of the x projections (register block)
-constexpr int QX_HALF_MAX = 32; // half-range order per side, at most
+constexpr int QX_HALF_MAX = 100; // half-range order per side, at most (Sec. IV uses 100 for Kn > 1)
 constexpr int QX_FULL_MAX = 100;  // half the full-range x order (order 2 x 100 = 200), at most
 constexpr int LXMAX = 2 * QX_FULL_MAX;  // orthonormal x polynomials of a projection, at most
 constexpr int QYMAX = 8;        // full-range order on y

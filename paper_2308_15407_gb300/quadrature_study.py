@@ -1,6 +1,6 @@
 """Velocity-quadrature studies of Sec. IV and App. A in the paper's geometry.
 
-  python -m paper_2308_15407_gb300.quadrature_study [table1|fullhalf|heatflux] [--cells-per-sigma 20]
+  python -m paper_2308_15407_gb300.quadrature_study [table1|fullhalf|heatflux|mfr] [--cells-per-sigma 20]
 
 table1    The convergence test behind the paper's Table 1: for each flow (Fourier with
           Delta T = 0.1, Couette with U_w = 1, Poiseuille with a_y = 0.001 in v^2/sigma),
@@ -13,6 +13,8 @@ fullhalf  App. A's comparison (R = 10, eta0 = 0.01): full-range orders 16 .. 200
           same reference, beside half-range orders.
 heatflux  Fourier flow (Delta T = 0.1): the heat flux q_x / n0 across the channel against the
           Knudsen number (varied through R at fixed eta0) for eta0 in {0.01, 0.1, 0.2}.
+mfr       The Poiseuille mass flow rate against Kn for the half-range orders 8, 16, 32, 64, and
+          100 above Kn = 1 (the orders of Sec. IV's mass-flow figure), R = 10, a_y = 0.001.
 
 Steady states in FP64 to per-step residual 1e-9 under a wall-clock cap; RET-FM contact value
 (the paper's); Q_y = 5 for the 2D flows.  Everything runs through the public binding; the
@@ -129,13 +131,58 @@ def heatflux(cells_per_sigma=20, cap_s=600.0, R_values=(2, 3, 4, 6, 10, 20), qx_
     return {"cells_per_sigma": cells_per_sigma, "qx_half": qx_half, "seconds": sec, "rows": rows}
 
 
+def mfr(cells_per_sigma=20, cap_s=600.0, R=10, kn_values=(0.1, 0.5, 1.0, 2.0, 5.0), orders=(8, 16, 32, 64),
+        q_large=100, window=1.0, rel=2e-5):
+    """G = mean of n u_y over the channel / a_y (channel-width units), the paper's m-dot/m-dot_0
+    (Sec. IV), for each (Kn, order).  FP32 storage.  Each instance's dt follows its largest
+    velocity (~22 thermal speeds at order 100), so a per-step residual is no common measure of
+    convergence; instead the batch is stepped in chunks covering at least `window` time units
+    of the smallest dt, and an instance counts as steady once G changed by less than `rel`
+    (relative) over its last chunk.  Stops when all are steady or at the wall-clock cap."""
+    import torch
+    from . import fdlb as F
+    from . import workloads as W
+    dicts, tags = [], []
+    for kn in kn_values:
+        eta0 = W.eta_for_knudsen(float(kn), R)
+        cps = max(cells_per_sigma, int(np.ceil(60 / (R - 1.0))))
+        for q in tuple(orders) + ((q_large,) if kn > 1.0 else ()):
+            dicts.append(W.paper_geometry(R, eta0, qx_half=q, cells_per_sigma=cps, precision="fp32",
+                                          flow="poiseuille", a_y=0.001, qy=4))
+            tags.append({"Kn_L": float(kn), "eta0": float(eta0), "qx_half": q})
+    s = F.Solver([F.Params(**d) for d in dicts])
+    dt = np.asarray(s.dt, dtype=float)
+    chunk = int(np.ceil(window / dt.min()))
+    G = lambda i: float(np.mean(s.moments(i)["n"] * s.moments(i)["uy"])) / dicts[i]["accel_y"]
+    prev = np.full(len(dicts), np.nan)
+    change = np.full(len(dicts), np.inf)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < cap_s:
+        s.step(chunk)
+        steps += chunk
+        cur = np.array([G(i) for i in range(len(dicts))])
+        change = np.abs(cur - prev) / np.abs(cur)
+        prev = cur
+        failed = s.status()[1] != F.ACTIVE
+        if np.all((change < rel) | failed):
+            break
+    sec = time.perf_counter() - t0
+    _, st, _ = s.status()
+    rows = [{**t, "G": float(prev[i]), "last_change": float(change[i]), "time_units": float(steps * dt[i]),
+             "steady": bool(change[i] < rel), "status": int(st[i])} for i, t in enumerate(tags)]
+    return {"R": R, "cells_per_sigma": cells_per_sigma, "steps": steps, "chunk": chunk, "seconds": sec,
+            "criterion": f"relative change of G < {rel} over a chunk of >= {window} time units", "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["table1", "fullhalf", "heatflux"])
+    ap.add_argument("what", choices=["table1", "fullhalf", "heatflux", "mfr"])
     ap.add_argument("--cells-per-sigma", type=int, default=20)
     ap.add_argument("--cap-s", type=float, default=900.0)
     a = ap.parse_args()
-    fn = {"table1": table1, "fullhalf": fullhalf, "heatflux": heatflux}[a.what]
+    fn = {"table1": table1, "fullhalf": fullhalf, "heatflux": heatflux, "mfr": mfr}[a.what]
     print(json.dumps(fn(a.cells_per_sigma, a.cap_s)), flush=True)
 
 

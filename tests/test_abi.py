@@ -46,7 +46,7 @@ def test_abi_version_and_struct(F):
 def test_parameter_validation(F):
     ok = F.Params(nx=50, qx_half=4, qy=4, qz=4, kn=0.1, eta0=0.1)
     assert F.workspace_bytes([ok]) > 0
-    bad = [dict(nx=4), dict(qx_half=0), dict(qx_half=33), dict(qy=1), dict(qz=2), dict(qy=0, qz=4),
+    bad = [dict(nx=4), dict(qx_half=0), dict(qx_half=101), dict(qy=1), dict(qz=2), dict(qy=0, qz=4),
            dict(eta0=0.5), dict(kn=0.0), dict(T_left=0.0), dict(qy=0, qz=0, U_left=0.1)]
     for kw in bad:
         p = F.Params(**{**ok.__dict__, **kw})
@@ -85,8 +85,9 @@ def test_null_context_calls_fail_cleanly(F):
 
 
 def test_x_quadrature_validation(F):
-    """Orders: half-range up to 32 per side (Table 1 of Sec. IV reaches 29), full-range up to 200
-    (App. A's comparison needs ~200); the full rule's tables hold 2 qx_half polynomials."""
+    """Orders: half-range up to 100 per side (Table 1 of Sec. IV reaches 29; the mass flow above
+    Kn = 1 uses 100), full-range up to 200 (App. A's comparison needs ~200); the full rule's
+    tables hold 2 qx_half polynomials."""
     base = dict(nx=64, qx_half=8, qy=4, qz=0, kn=0.1, eta0=0.1)
     b_half = F.workspace_bytes([F.Params(**base)])
     b_full = F.workspace_bytes([F.Params(**base, x_quadrature="full")])
@@ -94,9 +95,9 @@ def test_x_quadrature_validation(F):
     assert F.workspace_bytes([F.Params(**{**base, "qx_half": 100}, x_quadrature="full")]) > 0
     with pytest.raises(F.FdlbError):
         F.workspace_bytes([F.Params(**{**base, "qx_half": 101}, x_quadrature="full")])
-    assert F.workspace_bytes([F.Params(**{**base, "qx_half": 32})]) > 0
+    assert F.workspace_bytes([F.Params(**{**base, "qx_half": 100})]) > 0
     with pytest.raises(F.FdlbError):
-        F.workspace_bytes([F.Params(**{**base, "qx_half": 33})])
+        F.workspace_bytes([F.Params(**{**base, "qx_half": 101})])
     lib = F.load()
     c = F.Params(**base).to_c()
     c.x_quadrature = 2
@@ -128,6 +129,19 @@ def test_library_half_range_rule_matches_oracle(F, Q):
     r = qd.half_range_rule(Q)
     np.testing.assert_allclose(x, r.nodes, rtol=2e-15, atol=1e-14)
     np.testing.assert_allclose(w, r.weights, rtol=5e-14, atol=1e-17)
+
+
+@pytest.mark.parametrize("Q", [32, 64, 100])
+def test_library_half_range_rule_high_orders(F, Q):
+    """The library's rules (Stieltjes on a discretised weight, compensated sums) at the orders of
+    Sec. IV's large-Kn runs, against the oracle's (decimal moments): nodes to ~1e-14 absolute,
+    weights to 3e-13 relative down to the smallest (~1e-107 at order 100)."""
+    x, w = F.quadrature("half", Q)
+    r = qd.half_range_rule(Q)
+    np.testing.assert_allclose(x, r.nodes, rtol=0, atol=2e-14)
+    np.testing.assert_allclose(w, r.weights, rtol=3e-13, atol=0)
+    with pytest.raises(F.FdlbError):
+        F.quadrature("half", 101)
 
 
 @pytest.mark.parametrize("Q", [2, 3, 4, 6, 8, 10, 12, 16])

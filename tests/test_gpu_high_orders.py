@@ -1,5 +1,6 @@
 """x quadratures beyond 16 per side: the half-range orders of Table 1 (Sec. IV, up to 29 per
-side) and full-range orders beyond 16 (App. A).  The closure's x projections then run in
+side), the orders of the mass-flow runs at large Kn (64, and 100 above Kn = 1, Sec. IV) and
+full-range orders beyond 16 (App. A).  The closure's x projections then run in
 blocks of 16 orthonormal polynomials (the chain of H products continuing across blocks), the
 auxiliary rule grows with the order, and the update loads only its chunk's x-projection rows.
 FP64 parity 1e-12 and FP32 1e-5 against the oracle, in one batch with a low-order instance;
@@ -50,3 +51,27 @@ def test_high_orders_resident_equals_tiled_bitwise():
         sa.step(n)
         sb.step(n)
         assert_same(sa, sb)
+
+
+# Sec. IV's mass-flow orders: 64 per side, and 100 per side above Kn = 1 (Fourier 1D and a
+# Poiseuille channel at Kn = 2), with a low-order instance in the same batch
+LARGE_KN = [
+    dict(nx=30, qx_half=64, qy=0, qz=0, kn=0.5, eta0=0.05, T_left=0.95, T_right=1.05),
+    dict(nx=24, qx_half=100, qy=0, qz=0, kn=2.0, eta0=0.02, T_left=1.05, T_right=0.95),
+    dict(nx=24, qx_half=100, qy=4, qz=0, kn=2.0, eta0=0.02, accel_y=0.05, flow=2),
+    dict(nx=45, qx_half=4, qy=4, qz=0, kn=0.1, eta0=0.1, U_left=-0.2, U_right=0.2),
+]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_orders_64_and_100_match_oracle(precision, tol):
+    F = lib()
+    ps = [F.Params(**d, precision=precision) for d in LARGE_KN]
+    s = F.Solver(ps)
+    s.set_schedule("tiled")
+    s.step(20)
+    for i, d in enumerate(LARGE_KN):
+        o = oracle_for(F.Params(**d))
+        assert abs(s.dt[i] - o.dt) <= 1e-14 * o.dt
+        o.step(20)
+        compare(s.moments(i), o.moments(), tol, f"instance {i} ({precision})")

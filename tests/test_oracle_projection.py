@@ -150,3 +150,24 @@ def test_full_projection_high_orders(Q):
             got = float(np.sum(P[a] * r.nodes ** s))
             scale = float(np.sum(np.abs(P[a]) * np.abs(r.nodes) ** s))
             assert abs(got - want[s]) <= 1e-12 * max(scale, 1.0), (a, s)
+
+
+@pytest.mark.parametrize("Q", [64, 100])
+def test_half_projection_orders_64_100(Q):
+    """Sec. IV's orders for the mass flow at large Kn: at rest the projection is the rule's
+    weights (to round-off of the largest weight; the outermost populations, ~1e-60 of the
+    largest, keep only absolute accuracy), and at moving states it reproduces the moments
+    s <= 8 -- those that carry n, u, T, q and Pi -- of the closed forms above."""
+    r = qd.half_range_rule(Q)
+    P0 = qd.project_half(r.nodes, 0.0, 1.0)[0]
+    assert np.max(np.abs(P0 - r.weights)) <= 1e-14 * r.weights.max()
+    big = r.weights > 1e-12 * r.weights.max()
+    np.testing.assert_allclose(P0[big], r.weights[big], rtol=1e-9)
+    p = r.nodes
+    for u, T in ((0.05, 0.95), (-0.3, 1.1)):
+        P = qd.project_half(p, u, T)
+        for a in range(4):
+            want = half_line_moments(u, T, 8, a)
+            for s in range(9):
+                got = float(np.sum(P[a] * p ** s))
+                assert abs(got - want[s]) <= 1e-13 * max(abs(want[s]), 1e-3), (a, s, got, want[s])

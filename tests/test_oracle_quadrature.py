@@ -65,3 +65,31 @@ def test_full_range_weights_paper_formula(Q):
         for l in range(1, Q + 1):
             he.append(x * he[l] - l * he[l - 1])
         assert abs(Decimal(math.factorial(Q)) / he[Q + 1] ** 2 - w) <= Decimal(10) ** -50 * w
+
+
+@pytest.mark.parametrize("Q", [64, 100])
+def test_half_range_high_orders(Q):
+    """The orders Sec. IV uses for the mass flow at large Kn (64, and 100 above Kn = 1): exact
+    moments below degree 2Q; at degree 2Q the rule misses by exactly the squared norm of the
+    monic pi_Q (it integrates p^2Q - pi_Q^2 exactly and pi_Q vanishes at the nodes), which pins
+    the nodes as the zeros of pi_Q (decimal); the weights of Eq. (hh_wk); and the float64
+    rule exact to round-off relative to the terms' magnitudes; the working precision grows with
+    the order (the moment route loses digits), which a 200-digit build would not reach."""
+    r = qd.half_range_rule(Q)
+    assert r.prec > 200
+    for s in range(0, 2 * Q, 3):
+        got = sum(w * x ** s for w, x in zip(r.weights_dec, r.nodes_dec))
+        assert abs(got - qd.half_range_moment(s)) <= Decimal(10) ** -60 * qd.half_range_moment(s)
+    got = sum(w * x ** (2 * Q) for w, x in zip(r.weights_dec, r.nodes_dec))
+    miss = qd.half_range_moment(2 * Q) - got
+    assert abs(miss - r.norms[Q]) <= Decimal(10) ** -40 * r.norms[Q]
+    aQ = r.ortho[Q + 1][Q + 1] / r.ortho[Q][Q]
+    s2pi = (2 * qd._pi()).sqrt()
+    for x, w in list(zip(r.nodes_dec, r.weights_dec))[::7]:
+        wp = x * aQ ** 2 / (r.eval_ortho(Q + 1, x) ** 2 * (x + r.eval_ortho(Q, Decimal(0)) ** 2 / s2pi))
+        assert abs(wp - w) <= Decimal(10) ** -40 * w
+    x, w = r.nodes, r.weights
+    assert np.all(np.diff(x) > 0) and np.all(w > 0)
+    for s in range(2 * Q):
+        got = np.sum(w * x ** s)
+        assert abs(got - float(qd.half_range_moment(s))) <= 1e-13 * np.sum(w * x ** s)
