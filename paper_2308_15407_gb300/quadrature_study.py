@@ -163,7 +163,6 @@ def mfr(cells_per_sigma=20, cap_s=600.0, R=10, kn_values=(0.1, 0.5, 1.0, 2.0, 5.
     convergence; instead the batch is stepped in chunks covering at least `window` time units
     of the smallest dt, and an instance counts as steady once G changed by less than `rel`
     (relative) over its last chunk.  Stops when all are steady or at the wall-clock cap."""
-    import torch
     from . import fdlb as F
     from . import workloads as W
     dicts, tags = [], []
@@ -183,13 +182,12 @@ def _step_until_steady(F, s, n, monitor, cap_s, window, rel):
     """Steps batch s in chunks of at least `window` time units of its smallest dt until, for
     every instance i, monitor(i) = (values, scale) changed by less than rel * scale (largest
     element) over the last chunk, or an instance failed, or the wall-clock cap.  Returns
-    (last values, last relative changes, steps, seconds, dt, steps per chunk)."""
-    import torch
+    (last values, last relative changes, steps, seconds, dt, steps per chunk).  The monitor's
+    reads of the moments synchronise with the device, so the clock is right at chunk ends."""
     dt = np.asarray(s.dt, dtype=float)
     chunk = int(np.ceil(window / dt.min()))
     prev = [None] * n
     change = np.full(n, np.inf)
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
     steps = 0
     while time.perf_counter() - t0 < cap_s:
