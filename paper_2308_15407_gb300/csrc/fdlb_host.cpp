@@ -64,9 +64,18 @@ struct fdlb_ctx {
     cudaStream_t stream2 = nullptr;   // created on first use of FDLB_SCHED_MIXED
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
-    // CUDA graph of GRAPH_STEPS steps for one freeze tolerance (replayed by fdlb_step)
+    // update blocks of 16 warps (the same results as 8) while the active instances' update blocks
+    // fit on the SMs at once: a 16-warp block holds a whole SM's registers, so with more blocks
+    // than SMs it would run in waves
+    int n_sms = 0;
+    std::vector<int> upd_blocks;      // update work items of each instance
+    bool upd_wide = false;            // in use: fdlb_step keeps the choice made at creation (all
+    bool upd_wide_all = false;        // instances active); fdlb_run re-chooses at each status check
+    // CUDA graph of GRAPH_STEPS steps for one freeze tolerance and update width (replayed by
+    // fdlb_step)
     cudaGraphExec_t graph = nullptr;
     double graph_tol = -1.0;
+    bool graph_wide = false;
     bool graph_failed = false;
     // optional per-kernel-class event timing (fdlb_profile)
     bool prof = false;
@@ -84,6 +93,7 @@ struct fdlb_ctx {
 
 static void choose_cluster(fdlb_ctx* c);
 static void choose_smem_resident(fdlb_ctx* c);
+static void choose_update_width(fdlb_ctx* c, const int* st);
 
 // Record a start/stop event pair around one launch of class `kind` when profiling is on.
 static cudaError_t prof_mark(fdlb_ctx* c, int kind) {
@@ -113,7 +123,7 @@ static cudaError_t step_once(fdlb_ctx* c, double freeze_tol) {
     for (int stage = 1; stage <= 3; ++stage) {
         guard(KK_NODAL, [&] { return launch_nodal(c->d_inst, c->d_nod, c->n_nod, c->qmax, c->stream); });
         guard(KK_UPDATE, [&] { return launch_update(c->d_inst, c->d_upd, c->n_upd, stage, c->smem_upd_f64, c->smem_upd_f32,
-                                                    c->any_fp64, c->any_fp32, c->stream); });
+                                                    c->any_fp64, c->any_fp32, c->upd_wide, c->stream); });
     }
     guard(KK_RESID, [&] { return launch_resid(c->d_inst, c->count, -2, freeze_tol, c->d_resid_all, c->stream); });
     return e;
@@ -847,16 +857,27 @@ extern "C" int fdlb_create(fdlb_ctx** out, const fdlb_params* params, int32_t co
         c->inst.push_back(I);
 
         int tiles = (N + TILE - 1) / TILE;
+        const size_t nu0 = wu.size();
         for (int t = 0; t < tiles; ++t) {
             for (int k0 = 0; k0 < L.K; k0 += L.ukc) wu.push_back({ii, t * TILE, k0, std::min(L.K, k0 + L.ukc)});
             for (int role = 0; role < 3; ++role) wn.push_back({ii, t * TILE, role, 0});
         }
+        c->upd_blocks.push_back((int)(wu.size() - nu0));
         c->qmax = std::max(c->qmax, Lx);      // register and shared arrays hold Lx polynomials
         c->ukc_max = std::max(c->ukc_max, L.ukc);
         if (p.precision != FDLB_FP32_STORAGE) max_smem64 = std::max(max_smem64, update_smem_bytes(L.trows, L.ukc, 8, 8)), c->any_fp64 = true;
         if (p.precision != FDLB_FP64) max_smem32 = std::max(max_smem32, update_smem_bytes(L.trows, L.ukc, 4, 4)), c->any_fp32 = true;
     }
     if (off > need) { delete c; return fail(nullptr, FDLB_EINVAL, "internal: workspace layout overflow"); }
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            c->n_sms = 0;             // unknown: 8-warp update blocks throughout
+        }
+        choose_update_width(c, nullptr);
+        c->upd_wide_all = c->upd_wide;
+    }
     c->smem_upd_f64 = max_smem64;
     c->smem_upd_f32 = max_smem32;
 
@@ -1029,7 +1050,7 @@ static int set_smem_flags(fdlb_ctx* c, bool on) {
 // Capture GRAPH_STEPS steps into an executable graph (kernels only; no host synchronisation
 // inside).  The legacy default stream cannot be captured: then steps are launched directly.
 static bool ensure_graph(fdlb_ctx* c, double tol) {
-    if (c->graph && c->graph_tol == tol) return true;
+    if (c->graph && c->graph_tol == tol && c->graph_wide == c->upd_wide) return true;
     if (c->graph_failed || c->stream == nullptr) return false;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     cudaGraph_t g = nullptr;
@@ -1056,7 +1077,16 @@ static bool ensure_graph(fdlb_ctx* c, double tol) {
         return false;
     }
     c->graph_tol = tol;
+    c->graph_wide = c->upd_wide;
     return true;
+}
+
+// Update width from the instances still active (st: statuses, null = all active).
+static void choose_update_width(fdlb_ctx* c, const int* st) {
+    long blocks = 0;
+    for (int i = 0; i < c->count; ++i)
+        if (!st || st[i] == FDLB_ACTIVE) blocks += c->upd_blocks[i];
+    c->upd_wide = c->n_sms > 0 && blocks <= c->n_sms;
 }
 
 static int step_tiled(fdlb_ctx* c, int64_t nsteps, double freeze_tol) {
@@ -1225,6 +1255,11 @@ extern "C" int fdlb_run(fdlb_ctx* c, double tol, int64_t max_steps, int64_t chec
     std::vector<int> st(c->count);
     std::vector<long long> steps(c->count);
     int64_t done = 0;
+    // the width chosen from the active instances holds only inside this call
+    struct RestoreWidth {
+        fdlb_ctx* c;
+        ~RestoreWidth() { c->upd_wide = c->upd_wide_all; }
+    } restore{c};
     while (true) {
         int rc = fdlb_status(c, nullptr, st.data(), nullptr);
         if (rc) return rc;
@@ -1244,6 +1279,7 @@ extern "C" int fdlb_run(fdlb_ctx* c, double tol, int64_t max_steps, int64_t chec
         }
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > timeout_s) return fail(c, FDLB_ETIMEOUT, "fdlb_run: wall-clock limit reached");
+        choose_update_width(c, st.data());
         int64_t chunk = std::min<int64_t>(check_every, max_steps - done);
         rc = fdlb_step(c, chunk, tol);
         if (rc) return rc;

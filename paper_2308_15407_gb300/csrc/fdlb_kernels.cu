@@ -1345,7 +1345,8 @@ __device__ __forceinline__ float weno_face(float a, float b, float c, float d, f
     return fmaf(w1 * is, F1, fmaf(w2 * is, F2, w3 * is * F3));
 }
 
-constexpr int UPD_WARPS = 8;
+constexpr int UPD_WARPS = 8;          // warps of an update block; the moment epilogue's partials
+constexpr int UPD_WARPS_WIDE = 16;    // wide update blocks: the velocity loop on 16 warps
 
 // ---------------------------------------------------------------------------
 // stochastic rounding of FP32 storage
@@ -1460,10 +1461,11 @@ __device__ __forceinline__ void load_tw(const Inst& I, void* tws, int tid, int n
 // the moments (one chunk per tile) or the chunk's partial sums in msum[grp].
 template <typename S>
 __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, const S* fo, double* ex, const void* tws,
-                              int lane, int wy) {
+                              int lane, int wy, int nwb = UPD_WARPS) {
     const int i = i0 + lane, ld = I.ld, Tc = I.Tc, Q = I.Q, G = I.mgroups;
     const bool valid = i < I.N;
-    // warp wy takes the velocities [ka, kb) of the chunk, cut at x-velocity boundaries
+    // warp wy < UPD_WARPS takes the velocities [ka, kb) of the chunk (warps beyond, in a wide
+    // block, take none and only join the cross-warp sums: the same arithmetic in any block)
     const int per = (k1 - k0 + UPD_WARPS - 1) / UPD_WARPS;
     const int ka = min(k1, k0 + wy * per), kb = min(k1, ka + per);
     double* ss = ex + UPD_WARPS * MOM_SUMS * TILE;
@@ -1496,10 +1498,11 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
             outer_sums_df(o, Sd, df_of(I.px2[kx]), kx >= Q);
         }
         float2* pe = reinterpret_cast<float2*>(ex);
+        if (wy < UPD_WARPS)
 #pragma unroll
-        for (int j = 0; j < MOM_SUMS; ++j) pe[(wy * MOM_SUMS + j) * TILE + lane] = make_float2(o[j].hi, o[j].lo);
+            for (int j = 0; j < MOM_SUMS; ++j) pe[(wy * MOM_SUMS + j) * TILE + lane] = make_float2(o[j].hi, o[j].lo);
         __syncthreads();
-        for (int j = wy; j < MOM_SUMS; j += UPD_WARPS) {
+        for (int j = wy; j < MOM_SUMS; j += nwb) {
             df v = {0.0f, 0.0f};
             for (int q = 0; q < UPD_WARPS; ++q) v = v + df_of(pe[(q * MOM_SUMS + j) * TILE + lane]);
             if (G > 1) {
@@ -1530,10 +1533,11 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
             for (int j = 0; j < NTW; ++j) Sv[j] = a[j].value();
             outer_sums(o, Sv, I.px[kx], kx >= Q);
         }
+        if (wy < UPD_WARPS)
 #pragma unroll
-        for (int j = 0; j < MOM_SUMS; ++j) ex[(wy * MOM_SUMS + j) * TILE + lane] = o[j];
+            for (int j = 0; j < MOM_SUMS; ++j) ex[(wy * MOM_SUMS + j) * TILE + lane] = o[j];
         __syncthreads();
-        for (int j = wy; j < MOM_SUMS; j += UPD_WARPS) {
+        for (int j = wy; j < MOM_SUMS; j += nwb) {
             double v = 0.0;
             for (int q = 0; q < UPD_WARPS; ++q) v += ex[(q * MOM_SUMS + j) * TILE + lane];
             if (G > 1) {
@@ -1553,7 +1557,7 @@ __device__ void chunk_moments(const Inst& I, int i0, int k0, int k1, int grp, co
 // (ticket) adds the chunks' partial sums in chunk order -- the result does not depend on the
 // arrival order -- and resets the ticket.  ss: MOM_SUMS x TILE shared doubles.
 template <typename S>
-__device__ void chunk_ticket_final(const Inst& I, int i0, double* ss) {
+__device__ void chunk_ticket_final(const Inst& I, int i0, double* ss, int nwb = UPD_WARPS) {
     __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, tile = i0 / TILE;
     __threadfence();
@@ -1563,7 +1567,7 @@ __device__ void chunk_ticket_final(const Inst& I, int i0, double* ss) {
     if (!last) return;
     __threadfence();
     if (tid == 0) I.mcnt[tile] = 0;
-    moments_final_tile<S>(I, i0, ss, tid, UPD_WARPS, 1);
+    moments_final_tile<S>(I, i0, ss, tid, nwb, 1);
 }
 
 // ---- bulk asynchronous copies into shared memory (cp.async.bulk with an mbarrier) ----
@@ -1603,7 +1607,8 @@ constexpr long COPY_WAIT_POLLS = 2000000;      // ~2 s at the suspend hint
 // moves a multiple of 16 bytes.  Returns false if the copies did not complete within the wait
 // limit (the instance is then marked FDLB_FAILED_COPY).
 template <typename S, bool BULK>
-__device__ bool stage_rows(const Inst& I, int i0, int k0, int nrows, int stage, S* Sw, S* Fo, int lane, int wy) {
+__device__ bool stage_rows(const Inst& I, int i0, int k0, int nrows, int stage, S* Sw, S* Fo, int lane, int wy,
+                           int nwb = UPD_WARPS) {
     const int ld = I.ld;
     const int lo = max(0, i0 - 4), hi = min(ld, i0 + 36);
     const int off = lo - (i0 - 4);
@@ -1622,7 +1627,7 @@ __device__ bool stage_rows(const Inst& I, int i0, int k0, int nrows, int stage, 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (lane == 0)
-            for (int r = wy; r < nrows; r += UPD_WARPS) {
+            for (int r = wy; r < nrows; r += nwb) {
                 bulk_g2s(Sw + r * SW + off, src + (size_t)(k0 + r) * ld + lo, rowbytes, &bar);
                 if (withF) bulk_g2s(Fo + r * TILE, F + (size_t)(k0 + r) * ld + i0, fbytes, &bar);
             }
@@ -1641,7 +1646,7 @@ __device__ bool stage_rows(const Inst& I, int i0, int k0, int nrows, int stage, 
     } else {
         __syncthreads();
         const int n = hi - lo;
-        for (int r = wy; r < nrows; r += UPD_WARPS) {
+        for (int r = wy; r < nrows; r += nwb) {
             const S* row = src + (size_t)(k0 + r) * ld + lo;
             for (int j = lane; j < n; j += TILE) Sw[r * SW + off + j] = row[j];
             if (withF) Fo[r * TILE + lane] = F[(size_t)(k0 + r) * ld + i0 + lane];
@@ -1651,12 +1656,14 @@ __device__ bool stage_rows(const Inst& I, int i0, int k0, int nrows, int stage, 
     }
 }
 
-// Velocities [k0, k1) of one tile for RK stage `stage`, by UPD_WARPS warps (lane, warp wy);
+// Velocities [k0, k1) of one tile for RK stage `stage`, by W warps (lane, warp wy; the
+// velocity loop on all W, the moment partials on UPD_WARPS of them, so that W = 8 and 16 give
+// the same results bit for bit);
 // smem_raw holds upd_smem_bytes(ntab, ukc, sizeof(C), sizeof(S)).  The chunk's source rows (and
 // F) are staged in shared memory first (stage_rows); the stencil, the ghost cells of the diffuse
 // walls and F are then read from there.  The epilogue computes the moments of the new values
 // (chunk_moments).  Returns false when the staging copies failed.
-template <typename S, typename C, bool BULK>
+template <typename S, typename C, bool BULK, int W = UPD_WARPS>
 __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, unsigned char* smem_raw, int lane, int wy) {
     C* stab = reinterpret_cast<C*>(smem_raw);
     void* tws = smem_raw + upd_table_bytes(I.trows, sizeof(C));
@@ -1676,14 +1683,14 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const C* gRc = Tabs<C>::gR(I);
     const C* Kyc = Tabs<C>::Ky(I);
     __syncthreads();                      // the previous item's readers of shared memory are done
-    if (!stage_rows<S, BULK>(I, i0, k0, k1 - k0, stage, Sw, fo, lane, wy)) return false;
+    if (!stage_rows<S, BULK>(I, i0, k0, k1 - k0, stage, Sw, fo, lane, wy, W)) return false;
     // rows in batches: all loads of a batch are issued before its shared-memory stores
     constexpr int TB = 16;
-    for (int r0 = wy; r0 < trows; r0 += UPD_WARPS * TB) {
+    for (int r0 = wy; r0 < trows; r0 += W * TB) {
         C tmp[TB];
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
-            const int r = r0 + b * UPD_WARPS;
+            const int r = r0 + b * W;
             int gr = -1;                              // row of the instance's table
             if (r < 4 * NKX) {
                 const int a = r / NKX, kx = kx0 + (r - a * NKX);
@@ -1695,11 +1702,11 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
         }
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
-            const int r = r0 + b * UPD_WARPS;
+            const int r = r0 + b * W;
             if (r < trows) stab[r * TILE + lane] = tmp[b];
         }
     }
-    load_tw<S>(I, tws, wy * TILE + lane, UPD_WARPS * TILE);
+    load_tw<S>(I, tws, wy * TILE + lane, W * TILE);
     __syncthreads();
     const S* src = static_cast<const S*>(I.f[stage - 1]);
     S* dst = static_cast<S*>(I.f[stage % 3]);
@@ -1716,9 +1723,9 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
     const C sixth = (C)(1.0 / 6.0);
     // every stencil node of the tile inside the domain: no ghost cells (block-uniform)
     const bool interior = i0 >= 3 && i0 + TILE + 3 <= N;
-    // (kx, t) of the warp's velocities k = k0 + wy + UPD_WARPS m, stepped without divisions
+    // (kx, t) of the warp's velocities k = k0 + wy + W m, stepped without divisions
     int kx = (k0 + wy) / Tc, t = (k0 + wy) - kx * Tc;
-    for (int k = k0 + wy; k < k1; k += UPD_WARPS) {
+    for (int k = k0 + wy; k < k1; k += W) {
         const bool pos = kx < Q;
         const C p = pxc[kx];
         // node values i-3 .. i+3 (staged node j at row index j - i0 + 4) with the ghost cells of
@@ -1793,27 +1800,28 @@ __device__ bool update_item(const Inst& I, int i0, int k0, int k1, int stage, un
         } else {
             *fk = (S)0;
         }
-        t += UPD_WARPS;
+        t += W;
         while (t >= Tc) {
             t -= Tc;
             ++kx;
         }
     }
     __syncthreads();                      // every warp is done with the staged rows (ex aliases them)
-    chunk_moments<S>(I, i0, k0, k1, k0 / I.ukc, fo, ex, tws, lane, wy);
+    chunk_moments<S>(I, i0, k0, k1, k0 / I.ukc, fo, ex, tws, lane, wy, W);
     return true;
 }
 
-template <typename S, typename C>
-__global__ void __launch_bounds__(TILE * UPD_WARPS) k_update(const Inst* __restrict__ insts, const Work* __restrict__ work, int stage) {
+template <typename S, typename C, int W>
+__global__ void __launch_bounds__(TILE * W) k_update(const Inst* __restrict__ insts, const Work* __restrict__ work, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
     const Work w = work[blockIdx.x];
     const Inst& I = insts[w.inst];
     if (*I.status != FDLB_ACTIVE || I.smem_res) return;
     if ((I.precision == FDLB_FP64) != (sizeof(S) == 8)) return;
-    if (!update_item<S, C, true>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y)) return;
-    if (I.mgroups > 1) chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_stage_offset(I.trows, sizeof(C))) + UPD_WARPS * MOM_SUMS * TILE);
+    if (!update_item<S, C, true, W>(I, w.i0, w.k0, w.k1, stage, smem_raw, threadIdx.x, threadIdx.y)) return;
+    if (I.mgroups > 1)
+        chunk_ticket_final<S>(I, w.i0, reinterpret_cast<double*>(smem_raw + upd_stage_offset(I.trows, sizeof(C))) + UPD_WARPS * MOM_SUMS * TILE, W);
 }
 
 // Moments of buffer `buf` from scratch (creation, new profiles, a loaded state): one block per
@@ -2080,11 +2088,15 @@ cudaError_t launch_resid(const Inst* d_inst, int count, int anchor_inst, double 
 static cudaError_t set_smem(DevAttr* A, size_t smem64, size_t smem32) {
     cudaError_t e = cudaSuccess;
     if (smem64 > 48 * 1024 && smem64 > A->upd64) {
-        e = cudaFuncSetAttribute(k_update<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+        e = cudaFuncSetAttribute(k_update<double, double, UPD_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_update<double, double, UPD_WARPS_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
         if (e == cudaSuccess) A->upd64 = smem64;
     }
     if (e == cudaSuccess && smem32 > 48 * 1024 && smem32 > A->upd32) {
-        e = cudaFuncSetAttribute(k_update<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        e = cudaFuncSetAttribute(k_update<float, float, UPD_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_update<float, float, UPD_WARPS_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e == cudaSuccess) A->upd32 = smem32;
     }
     return e;
@@ -2233,11 +2245,18 @@ cudaError_t launch_smemres(Inst* d_inst, const int* d_list, int n, int qmax, siz
 }
 
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
-                          bool f64, bool f32, cudaStream_t s) {
-    dim3 blk(TILE, UPD_WARPS);
+                          bool f64, bool f32, bool wide, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    if (f64) e = launch_pdl(k_update<double, double>, (unsigned)n_upd, blk, smem64, s, d_inst, d_upd, stage);
-    if (e == cudaSuccess && f32) e = launch_pdl(k_update<float, float>, (unsigned)n_upd, blk, smem32, s, d_inst, d_upd, stage);
+    if (wide) {
+        const dim3 blk(TILE, UPD_WARPS_WIDE);
+        if (f64) e = launch_pdl(k_update<double, double, UPD_WARPS_WIDE>, (unsigned)n_upd, blk, smem64, s, d_inst, d_upd, stage);
+        if (e == cudaSuccess && f32)
+            e = launch_pdl(k_update<float, float, UPD_WARPS_WIDE>, (unsigned)n_upd, blk, smem32, s, d_inst, d_upd, stage);
+    } else {
+        const dim3 blk(TILE, UPD_WARPS);
+        if (f64) e = launch_pdl(k_update<double, double, UPD_WARPS>, (unsigned)n_upd, blk, smem64, s, d_inst, d_upd, stage);
+        if (e == cudaSuccess && f32) e = launch_pdl(k_update<float, float, UPD_WARPS>, (unsigned)n_upd, blk, smem32, s, d_inst, d_upd, stage);
+    }
     return e;
 }
 

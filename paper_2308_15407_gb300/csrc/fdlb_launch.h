@@ -29,9 +29,10 @@ cudaError_t launch_set_profiles(const Inst* d_inst, int inst, cudaStream_t s);
 // Per-node closure (chi, Pr, tau, gradients, projection tables, wall densities).
 cudaError_t launch_nodal(const Inst* d_inst, const Work* d_nod, int n_nod, int qmax, cudaStream_t s);
 
-// RK stage `stage` (1..3) update of every ACTIVE instance.
+// RK stage `stage` (1..3) update of every ACTIVE instance; wide: blocks of 16 warps instead of
+// 8 (the same results bit for bit; faster when the active blocks fit on the SMs at once).
 cudaError_t launch_update(const Inst* d_inst, const Work* d_upd, int n_upd, int stage, size_t smem64, size_t smem32,
-                          bool f64, bool f32, cudaStream_t s);
+                          bool f64, bool f32, bool wide, cudaStream_t s);
 
 // Resident schedule: attributes (shared memory, cluster size cs) of the cluster kernel for
 // the batch's largest half-range order and update-item shared memory; *smem receives its
