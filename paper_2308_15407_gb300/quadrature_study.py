@@ -7,8 +7,9 @@ table1    The convergence test behind the paper's Table 1: for each flow (Fourie
           confinement R in {4, 10} and reduced density eta0 in {0.01, 0.1, 0.2}, the error
           eps = max |M - M_ref| / (max M_ref - min M_ref) (M = T, u_y, u_y) of half-range orders
           4 .. 29 per side against a reference, and the smallest order with eps < 1 %.  The
-          paper's reference is order 200 and its spacing sigma/100; here the reference is the
-          library's largest half-range order, 32 per side, and the spacing is an argument.
+          paper's reference is order 200 and its spacing sigma/100; here the reference is
+          32 per side, and the spacing is an argument.  --flows / --etas select a subset,
+          --steady profile stops on the change of the profiles instead of the residual.
 fullhalf  App. A's comparison (R = 10, eta0 = 0.01): full-range orders 16 .. 200 against the
           same reference, beside half-range orders.
 heatflux  Fourier flow (Delta T = 0.1): the heat flux q_x / n0 across the channel against the
@@ -18,9 +19,12 @@ mfr       The Poiseuille mass flow rate against Kn for the half-range orders 8, 
 mfr_kn    The mass flow rate against Kn for R in {2, 5, 10, 20} as Sec. IV computes it: order 8
           up to Kn = 1, order 100 above (Kn = 2 and 5 here, with order 8 beside them).
 
-Steady states in FP64 to per-step residual 1e-9 under a wall-clock cap; RET-FM contact value
-(the paper's); Q_y = 5 for the 2D flows.  Everything runs through the public binding; the
-output is one JSON document.
+Steady states: table1, fullhalf and heatflux in FP64 to per-step residual 1e-9 under a
+wall-clock cap (table1 optionally by the change of its profiles); mfr and mfr_kn in FP32 by the
+change of the mass flow over a time unit (the per-step residual stops those flows early, since
+dt shrinks with the largest velocity of the order).  RET-FM contact value (the paper's); Q_y =
+5 for table1's 2D flows, 4 for the mass-flow runs.  Everything runs through the public binding;
+the output is one JSON document.
 """
 from __future__ import annotations
 
