@@ -144,6 +144,16 @@ def test_library_half_range_rule_high_orders(F, Q):
         F.quadrature("half", 101)
 
 
+@pytest.mark.parametrize("Q", [100, 200])
+def test_library_full_range_rule_high_orders(F, Q):
+    """The full-range orders of App. A's comparison (up to 200): nodes to 1e-14 absolute, weights
+    to 1e-13 relative down to the smallest (~1e-163 at order 200)."""
+    x, w = F.quadrature("full", Q)
+    r = qd.full_range_rule(Q)
+    np.testing.assert_allclose(x, r.nodes, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(w, r.weights, rtol=1e-13, atol=0)
+
+
 @pytest.mark.parametrize("Q", [2, 3, 4, 6, 8, 10, 12, 16])
 def test_library_full_range_rule_matches_oracle(F, Q):
     x, w = F.quadrature("full", Q)

@@ -171,3 +171,21 @@ def test_half_projection_orders_64_100(Q):
             for s in range(9):
                 got = float(np.sum(P[a] * p ** s))
                 assert abs(got - want[s]) <= 1e-13 * max(abs(want[s]), 1e-3), (a, s, got, want[s])
+
+
+@pytest.mark.parametrize("Q", [100, 200])
+def test_full_projection_orders_100_200(Q):
+    """App. A's orders up to 200: at rest the projection is the rule's weights (to round-off of
+    the largest), and at a moving state it reproduces the moments s <= 8 of the closed forms
+    (to round-off of the summed terms' magnitudes)."""
+    r = qd.full_range_rule(Q)
+    P0 = qd.project_full(r.nodes, 0.0, 1.0)[0]
+    assert np.max(np.abs(P0 - r.weights)) <= 1e-14 * r.weights.max()
+    u, T = 0.3, 1.05
+    P = qd.project_full(r.nodes, u, T)
+    for a in range(4):
+        want = full_line_moments(u, T, 8, a)
+        for s in range(9):
+            got = float(np.sum(P[a] * r.nodes ** s))
+            scale = float(np.sum(np.abs(P[a]) * np.abs(r.nodes) ** s))
+            assert abs(got - want[s]) <= 1e-13 * max(scale, abs(want[s])), (a, s, got, want[s])
