@@ -969,7 +969,11 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = i0 + lane;
     __syncthreads();                      // the previous item's readers of nsm are done
-    if (fp32 && role < 2) {
+    // FP32 storage: the half-range x projection in double-float.  A full-range x rule keeps the
+    // FP64 projection below (writing the FP32 table): its auxiliary Gauss-Hermite rule of
+    // Q_x^h + 2 points reaches |q| ~ 19 at order 200, where the orthonormal polynomials grow to
+    // ~e^(q^2/4) ~ 1e40, past the float range of the double-float recurrence.
+    if (fp32 && role < 2 && !I.xfull) {
         xproj_df<QB>(I, i0, role, nsm);
         return;
     }
