@@ -969,11 +969,13 @@ __device__ void nodal_item(const Inst& I, int i0, int role, double* nsm, bool fp
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = i0 + lane;
     __syncthreads();                      // the previous item's readers of nsm are done
-    // FP32 storage: the half-range x projection in double-float.  A full-range x rule keeps the
-    // FP64 projection below (writing the FP32 table): its auxiliary Gauss-Hermite rule of
-    // Q_x^h + 2 points reaches |q| ~ 19 at order 200, where the orthonormal polynomials grow to
-    // ~e^(q^2/4) ~ 1e40, past the float range of the double-float recurrence.
-    if (fp32 && role < 2 && !I.xfull) {
+    // FP32 storage: the half-range x projection in double-float, up to 32 polynomials.  Larger
+    // orders keep the FP64 projection below (writing the FP32 table): the orthonormal
+    // polynomials grow to ~e^(x^2/4) at the auxiliary points x = sqrt(T) q, beyond the float
+    // range (3e38) once x > ~18.8 -- the full-range rule of order 200 has |q| up to ~19, the
+    // half-range aux rule of order 100 q up to ~17 (overflow from T ~ 1.2); at 32 polynomials
+    // the aux rule ends near q = 11, which would need T > 3.
+    if (fp32 && role < 2 && !I.xfull && I.Lx <= 32) {
         xproj_df<QB>(I, i0, role, nsm);
         return;
     }
